@@ -1,0 +1,379 @@
+"""Seeded synthetic inputs: graphs in symmetric CSR form and initial eigenvector blocks.
+
+This module produces input data only. It holds none of the method's arithmetic (no Laplacian,
+no polynomial, no solver); both the FP64 oracle and the CUDA path read what it writes.
+
+Graph conventions (shared by every consumer):
+  * undirected, no self-loops, no duplicate edges;
+  * stored as a symmetric CSR: ``row_ptr`` (n+1, int32), ``col_idx`` (nnz, int32), columns
+    sorted ascending inside each row; ``w`` (nnz, float32) or ``None`` for unit weights;
+  * a weighted graph carries one weight per undirected edge, written to both directions.
+
+Workload families follow the paper's experiments (all synthetic in the paper too): stochastic
+block models and planted clusters (Section 5.4, Appendix A.1), the 3-room grid world
+(Section 5.3), and closed-form graphs used to pin the oracle (path, cycle, complete, star,
+grid, disjoint cliques; Section 2).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+__all__ = [
+    "CSRGraph", "from_edges", "path", "cycle", "complete", "star", "grid", "cliques",
+    "sbm", "sbm_by_degree", "chung_lu_clusters", "batched_sbm", "concat_graphs",
+    "random_graph", "three_room_grid", "gaussian_block", "uniform_edge_weights",
+    "undirected_edges", "DEFAULT_SEED",
+]
+
+DEFAULT_SEED = 20220729
+
+
+@dataclasses.dataclass
+class CSRGraph:
+    n: int
+    row_ptr: np.ndarray          # int32 [n+1]
+    col_idx: np.ndarray          # int32 [nnz]
+    w: np.ndarray | None = None  # float32 [nnz] or None (unit weights)
+    labels: np.ndarray | None = None  # planted block of each node, if any
+    name: str = ""
+
+    @property
+    def nnz(self) -> int:
+        return int(self.row_ptr[-1])
+
+    @property
+    def n_edges(self) -> int:
+        return self.nnz // 2
+
+    def degrees(self) -> np.ndarray:
+        """Number of stored neighbours per row (not the weighted degree)."""
+        return np.diff(self.row_ptr.astype(np.int64))
+
+    def max_count_degree(self) -> int:
+        return int(self.degrees().max()) if self.n else 0
+
+
+def from_edges(n: int, a, b, w=None, labels=None, name: str = "") -> CSRGraph:
+    """Build a symmetric CSR from undirected edge endpoint arrays.
+
+    Self-loops are dropped; duplicates of an undirected edge are merged, keeping the first
+    weight in input order (the input-hygiene reading for unspecified inputs).
+    """
+    a = np.asarray(a, dtype=np.int64).ravel()
+    b = np.asarray(b, dtype=np.int64).ravel()
+    keep = a != b
+    a, b = a[keep], b[keep]
+    if w is not None:
+        w = np.asarray(w, dtype=np.float32).ravel()[keep]
+    lo = np.minimum(a, b)
+    hi = np.maximum(a, b)
+    key = lo * np.int64(n) + hi
+    _, first = np.unique(key, return_index=True)
+    first.sort()
+    lo, hi = lo[first], hi[first]
+    if w is not None:
+        w = w[first]
+    rows = np.concatenate([lo, hi])
+    cols = np.concatenate([hi, lo])
+    order = np.argsort(rows * np.int64(n) + cols, kind="stable")
+    rows, cols = rows[order], cols[order]
+    counts = np.bincount(rows, minlength=n)
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(counts, out=row_ptr[1:])
+    if row_ptr[-1] > np.iinfo(np.int32).max:
+        raise ValueError("nnz exceeds int32 indexing")
+    ww = None
+    if w is not None:
+        ww = np.concatenate([w, w])[order].astype(np.float32)
+    return CSRGraph(n=n, row_ptr=row_ptr.astype(np.int32), col_idx=cols.astype(np.int32),
+                    w=ww, labels=None if labels is None else np.asarray(labels, np.int32),
+                    name=name)
+
+
+def undirected_edges(g: CSRGraph):
+    """(a, b, w) for every undirected edge with a < b, in CSR order of row a."""
+    rows = np.repeat(np.arange(g.n, dtype=np.int64), g.degrees())
+    cols = g.col_idx.astype(np.int64)
+    up = rows < cols
+    w = None if g.w is None else g.w[up]
+    return rows[up], cols[up], w
+
+
+# ----------------------------------------------------------------------------------------
+# closed-form graphs (their Laplacian spectra are known; used to pin the oracle)
+# ----------------------------------------------------------------------------------------
+def path(n: int) -> CSRGraph:
+    i = np.arange(n - 1)
+    return from_edges(n, i, i + 1, name=f"path{n}")
+
+
+def cycle(n: int) -> CSRGraph:
+    i = np.arange(n)
+    return from_edges(n, i, (i + 1) % n, name=f"cycle{n}")
+
+
+def complete(n: int) -> CSRGraph:
+    a, b = np.triu_indices(n, 1)
+    return from_edges(n, a, b, name=f"K{n}")
+
+
+def star(n: int) -> CSRGraph:
+    i = np.arange(1, n)
+    return from_edges(n, np.zeros(n - 1, np.int64), i, name=f"star{n}")
+
+
+def grid(rows: int, cols: int) -> CSRGraph:
+    idx = np.arange(rows * cols).reshape(rows, cols)
+    a = np.concatenate([idx[:, :-1].ravel(), idx[:-1, :].ravel()])
+    b = np.concatenate([idx[:, 1:].ravel(), idx[1:, :].ravel()])
+    return from_edges(rows * cols, a, b, name=f"grid{rows}x{cols}")
+
+
+def cliques(sizes, short_circuit: int = 0, seed: int = DEFAULT_SEED) -> CSRGraph:
+    """Disjoint cliques, optionally joined by ``short_circuit`` random inter-clique edges
+    (the Section 5.4 generator joins cliques by 0 to 25 such edges)."""
+    rng = np.random.default_rng(seed)
+    sizes = [int(s) for s in sizes]
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    a_list, b_list, lab = [], [], []
+    for c, s in enumerate(sizes):
+        aa, bb = np.triu_indices(s, 1)
+        a_list.append(aa + off[c])
+        b_list.append(bb + off[c])
+        lab.append(np.full(s, c))
+    n = int(off[-1])
+    labels = np.concatenate(lab)
+    if short_circuit and len(sizes) > 1:
+        got = 0
+        ea, eb = [], []
+        while got < short_circuit:
+            u = rng.integers(0, n, size=4 * short_circuit)
+            v = rng.integers(0, n, size=4 * short_circuit)
+            m = labels[u] != labels[v]
+            u, v = u[m], v[m]
+            take = min(len(u), short_circuit - got)
+            ea.append(u[:take])
+            eb.append(v[:take])
+            got += take
+        a_list += ea
+        b_list += eb
+    return from_edges(n, np.concatenate(a_list), np.concatenate(b_list), labels=labels,
+                      name=f"cliques{sizes}")
+
+
+# ----------------------------------------------------------------------------------------
+# random workloads
+# ----------------------------------------------------------------------------------------
+def _pairs_within(rng, starts, sizes, m):
+    """m uniform ordered pairs (u, v), u != v mostly, inside blocks given per draw."""
+    u = starts + (rng.random(m) * sizes).astype(np.int64)
+    v = starts + (rng.random(m) * sizes).astype(np.int64)
+    return u, v
+
+
+def sbm(n: int, n_blocks: int, p_in: float, p_out: float, seed: int = DEFAULT_SEED,
+        permute: bool = False) -> CSRGraph:
+    """Stochastic block model with equal blocks (the last one takes the remainder).
+
+    Edge counts are drawn from the exact binomials of the model; endpoints are drawn
+    uniformly inside the pair class and duplicates merged, which for sparse graphs differs
+    from the exact model only by the O(m^2/pairs) merged duplicates.
+    """
+    rng = np.random.default_rng(seed)
+    base = n // n_blocks
+    sizes = np.full(n_blocks, base, dtype=np.int64)
+    sizes[-1] += n - base * n_blocks
+    starts = np.concatenate([[0], np.cumsum(sizes)[:-1]])
+    labels = np.repeat(np.arange(n_blocks), sizes)
+    intra_pairs = sizes * (sizes - 1) // 2
+    m_in = rng.binomial(intra_pairs, p_in)
+    blk = np.repeat(np.arange(n_blocks), m_in)
+    u_in, v_in = _pairs_within(rng, starts[blk], sizes[blk], int(m_in.sum()))
+    total_pairs = n * (n - 1) // 2
+    inter_pairs = total_pairs - int(intra_pairs.sum())
+    m_out = int(rng.binomial(inter_pairs, p_out)) if inter_pairs > 0 else 0
+    ua, va = [], []
+    got = 0
+    while got < m_out:
+        need = m_out - got
+        u = rng.integers(0, n, size=int(need * 1.2) + 16)
+        v = rng.integers(0, n, size=int(need * 1.2) + 16)
+        keep = labels[u] != labels[v]
+        u, v = u[keep][:need], v[keep][:need]
+        ua.append(u)
+        va.append(v)
+        got += len(u)
+    a = np.concatenate([u_in] + ua) if ua else u_in
+    b = np.concatenate([v_in] + va) if va else v_in
+    g = from_edges(n, a, b, labels=labels, name=f"sbm{n}x{n_blocks}")
+    if permute:
+        g = _permute(g, rng.permutation(n))
+    return g
+
+
+def sbm_by_degree(n: int, n_blocks: int, mean_degree: float, intra_frac: float,
+                  seed: int = DEFAULT_SEED) -> CSRGraph:
+    """SBM parameterised by mean degree and the fraction of intra-block edge ends."""
+    base = max(n // n_blocks, 2)
+    p_in = min(1.0, mean_degree * intra_frac / max(base - 1, 1))
+    rest = max(n - base, 1)
+    p_out = min(1.0, mean_degree * (1.0 - intra_frac) / rest)
+    return sbm(n, n_blocks, p_in, p_out, seed=seed)
+
+
+def _permute(g: CSRGraph, perm: np.ndarray) -> CSRGraph:
+    a, b, w = undirected_edges(g)
+    inv = np.empty_like(perm)
+    inv[perm] = np.arange(len(perm))
+    lab = None
+    if g.labels is not None:
+        lab = np.empty_like(g.labels)
+        lab[inv] = g.labels
+    return from_edges(g.n, inv[a], inv[b], w=w, labels=lab, name=g.name + "-perm")
+
+
+def random_graph(n: int, m: int, seed: int = DEFAULT_SEED, hub: int | None = None,
+                 hub_degree: int = 0, isolated: int = 0) -> CSRGraph:
+    """Uniform random multigraph merged to a simple graph, with optional hub and isolated
+    nodes (ragged rows, empty rows and one long row for kernel edge cases)."""
+    rng = np.random.default_rng(seed)
+    live = n - isolated
+    a = rng.integers(0, live, size=m)
+    b = rng.integers(0, live, size=m)
+    if hub is not None and hub_degree:
+        hb = rng.choice(live, size=min(hub_degree, live), replace=False)
+        a = np.concatenate([a, np.full(len(hb), hub)])
+        b = np.concatenate([b, hb])
+    return from_edges(n, a, b, name=f"rand{n}_{m}")
+
+
+def chung_lu_clusters(n: int, n_clusters: int = 64, gamma: float = 2.5, d_min: float = 4.0,
+                      d_max: float = 1e4, sigma: float = 1.0, intra_frac: float = 0.9,
+                      target_nnz: float | None = None, weighted: bool = True,
+                      seed: int = DEFAULT_SEED) -> CSRGraph:
+    """Planted-cluster Chung-Lu graph: expected degrees from a power law with exponent
+    ``gamma`` on [d_min, d_max], clusters of log-normal sizes, a fraction ``intra_frac`` of
+    edge ends inside the cluster. Nodes are ordered by cluster. Weights U(0.5, 1.5)."""
+    rng = np.random.default_rng(seed)
+    e = 1.0 - gamma
+    u = rng.random(n)
+    theta = (d_min ** e - u * (d_min ** e - d_max ** e)) ** (1.0 / e)
+    if target_nnz is not None:
+        theta *= target_nnz / theta.sum()
+    sz = rng.lognormal(0.0, sigma, size=n_clusters)
+    sz = np.maximum(1, np.floor(sz / sz.sum() * n)).astype(np.int64)
+    sz[-1] += n - sz.sum()
+    if sz[-1] < 1:
+        raise ValueError("cluster sizes do not fit n")
+    off = np.concatenate([[0], np.cumsum(sz)])
+    labels = np.repeat(np.arange(n_clusters), sz)
+    cum = np.cumsum(theta)
+    total = cum[-1]
+    a_list, b_list = [], []
+    # intra-cluster edges: endpoints drawn proportional to theta inside the cluster
+    s_c = np.array([cum[off[c + 1] - 1] - (cum[off[c] - 1] if off[c] > 0 else 0.0)
+                    for c in range(n_clusters)])
+    m_c = rng.poisson(intra_frac * s_c / 2.0)
+    for c in range(n_clusters):
+        if m_c[c] == 0 or sz[c] < 2:
+            continue
+        lo = cum[off[c] - 1] if off[c] > 0 else 0.0
+        r1 = lo + rng.random(m_c[c]) * s_c[c]
+        r2 = lo + rng.random(m_c[c]) * s_c[c]
+        a_list.append(np.minimum(np.searchsorted(cum, r1, side="right"), off[c + 1] - 1))
+        b_list.append(np.minimum(np.searchsorted(cum, r2, side="right"), off[c + 1] - 1))
+    m_out = int(rng.poisson((1.0 - intra_frac) * total / 2.0))
+    if m_out:
+        r1 = rng.random(m_out) * total
+        r2 = rng.random(m_out) * total
+        ua = np.minimum(np.searchsorted(cum, r1, side="right"), n - 1)
+        va = np.minimum(np.searchsorted(cum, r2, side="right"), n - 1)
+        keep = labels[ua] != labels[va]
+        a_list.append(ua[keep])
+        b_list.append(va[keep])
+    a = np.concatenate(a_list)
+    b = np.concatenate(b_list)
+    w = rng.uniform(0.5, 1.5, size=len(a)).astype(np.float32) if weighted else None
+    return from_edges(n, a, b, w=w, labels=labels, name=f"chunglu{n}")
+
+
+def batched_sbm(n_graphs: int, n_min: int = 200, n_max: int = 20000, blocks_min: int = 2,
+                blocks_max: int = 8, mean_degree: float = 12.0, intra_frac: float = 0.875,
+                seed: int = DEFAULT_SEED):
+    """Independent SBMs of log-uniform size and a random number of blocks each."""
+    rng = np.random.default_rng(seed)
+    sizes = np.exp(rng.uniform(math.log(n_min), math.log(n_max), size=n_graphs)).astype(int)
+    nb = rng.integers(blocks_min, blocks_max + 1, size=n_graphs)
+    seeds = rng.integers(0, 2**62, size=n_graphs)
+    return [sbm_by_degree(int(sizes[i]), int(nb[i]), mean_degree, intra_frac, seed=int(seeds[i]))
+            for i in range(n_graphs)]
+
+
+def concat_graphs(graphs):
+    """Block-diagonal union: returns (graph, node_offsets[int64, G+1], nnz_offsets[G+1])."""
+    node_off = np.zeros(len(graphs) + 1, dtype=np.int64)
+    nnz_off = np.zeros(len(graphs) + 1, dtype=np.int64)
+    for i, g in enumerate(graphs):
+        node_off[i + 1] = node_off[i] + g.n
+        nnz_off[i + 1] = nnz_off[i] + g.nnz
+    rp = np.empty(node_off[-1] + 1, dtype=np.int64)
+    rp[0] = 0
+    cols = np.empty(nnz_off[-1], dtype=np.int64)
+    ws = None if graphs[0].w is None else np.empty(nnz_off[-1], dtype=np.float32)
+    for i, g in enumerate(graphs):
+        rp[node_off[i] + 1: node_off[i + 1] + 1] = g.row_ptr[1:].astype(np.int64) + nnz_off[i]
+        cols[nnz_off[i]: nnz_off[i + 1]] = g.col_idx.astype(np.int64) + node_off[i]
+        if ws is not None:
+            ws[nnz_off[i]: nnz_off[i + 1]] = g.w
+    if rp[-1] > np.iinfo(np.int32).max:
+        raise ValueError("nnz exceeds int32 indexing")
+    big = CSRGraph(n=int(node_off[-1]), row_ptr=rp.astype(np.int32),
+                   col_idx=cols.astype(np.int32), w=ws, name=f"batch{len(graphs)}")
+    return big, node_off, nnz_off
+
+
+def three_room_grid(s: int = 2, h: int = 10) -> CSRGraph:
+    """3-room grid world of Section 5.3: (10s+1) x (30s+1) cells, two inner walls splitting it
+    into three rooms, each wall with one door of height about (10s+1)/h cells (centred).
+    The wall geometry is not drawn in the text; this reading places full-height walls at
+    one and two thirds of the width."""
+    H, W = 10 * s + 1, 30 * s + 1
+    walls = {W // 3, (2 * W) // 3}
+    door = max(1, round(H / h))
+    d0 = (H - door) // 2
+    free = np.ones((H, W), dtype=bool)
+    for c in walls:
+        free[:, c] = False
+        free[d0:d0 + door, c] = True
+    idx = -np.ones((H, W), dtype=np.int64)
+    idx[free] = np.arange(free.sum())
+    a, b = [], []
+    for r in range(H):
+        for c in range(W):
+            if not free[r, c]:
+                continue
+            if c + 1 < W and free[r, c + 1]:
+                a.append(idx[r, c]); b.append(idx[r, c + 1])
+            if r + 1 < H and free[r + 1, c]:
+                a.append(idx[r, c]); b.append(idx[r + 1, c])
+    return from_edges(int(free.sum()), a, b, name=f"3room_s{s}_h{h}")
+
+
+# ----------------------------------------------------------------------------------------
+# vectors and weights
+# ----------------------------------------------------------------------------------------
+def gaussian_block(n: int, k: int, seed: int = DEFAULT_SEED) -> np.ndarray:
+    """V0 with i.i.d. N(0,1) entries (float64, row-major n x k)."""
+    return np.random.default_rng(seed).standard_normal((n, k))
+
+
+def uniform_edge_weights(g: CSRGraph, lo: float = 0.5, hi: float = 1.5,
+                         seed: int = DEFAULT_SEED) -> CSRGraph:
+    """Same graph with one U(lo, hi) float32 weight per undirected edge."""
+    a, b, _ = undirected_edges(g)
+    w = np.random.default_rng(seed).uniform(lo, hi, size=len(a)).astype(np.float32)
+    out = from_edges(g.n, a, b, w=w, labels=g.labels, name=g.name + "-w")
+    return out
