@@ -1,0 +1,428 @@
+"""Benchmark of the SPED hot path on one GB300 (or N replicas, one per GPU).
+
+Workload (default): stochastic block model, N = 1,000,000 nodes in 20 equal blocks, mean degree
+16 (14 inside the block, 2 outside), unweighted, k = 20. One step = one mixed-precision dilated
+solver step: p(L) V by the limit form (I - sL)^l chained in BF16 (first step reads the F32
+master, last step writes F32), the 2k x 2k Gram [V Y]^T [V Y], the k x k FP64 mu-EG algebra and the
+N x k update. Value = algorithmic HBM bytes of the step / device time (GB/s).
+
+Also measured: the dominant kernel (one chain step) against the HBM roofline, the end-to-end
+rate through the C ABI with host buffers, time-to-bottom-k (largest principal angle <= 1e-3)
+for the dilated mixed-precision solver against the plain-L FP64 solver, and the FP64 CPU oracle.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import gen  # noqa: E402
+
+METRIC = "time-to-bottom-k (angle≤1e-3) dilated vs plain L; p(L)·V HBM GB/s vs roofline"
+WORKLOAD = dict(n=1_000_000, blocks=20, p_in=14 / 49_999, p_out=2 / 950_000, k=20, ell=41)
+SEED = gen.DEFAULT_SEED
+
+
+def make_graph():
+    w = WORKLOAD
+    return gen.sbm(w["n"], w["blocks"], w["p_in"], w["p_out"], seed=SEED)
+
+
+def spmm_bytes(n, nnz, k, b_in, b_out, weighted=False):
+    """Algorithmic bytes of one chain step: row pointers, column indices (+ weights), the
+    input block read once, the output block written once (k columns, not the padding)."""
+    return 4 * (n + 1) + 4 * nnz + (4 * nnz if weighted else 0) + n * k * b_in + n * k * b_out
+
+
+def step_bytes(n, nnz, k, ell):
+    """One mixed-precision dilated solver step (F32 master V, BF16 chain, F32 Y)."""
+    chain = spmm_bytes(n, nnz, k, 4, 2) + (ell - 2) * spmm_bytes(n, nnz, k, 2, 2) + \
+        spmm_bytes(n, nnz, k, 2, 4)
+    gram = n * k * 4 * 2
+    update = n * k * 4 * 3
+    return chain, chain + gram + update
+
+
+# ----------------------------------------------------------------------------------------
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def _kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ["paper_2207_14589_gb300/csrc/spmm.cu", "paper_2207_14589_gb300/csrc/sped_internal.cuh"]:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _ncu_traffic():
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "step_rowgroup_bf16_sbm1e6_k20.md")
+    if not os.path.exists(p):
+        return None
+    txt = open(p).read()
+    m = re.search(r"source hash:\s*([0-9a-f]+)", txt)
+    t = re.search(r"traffic per launch \(bytes\):\s*([0-9.eE+]+)", txt)
+    if not m or not t or m.group(1) != _kernel_source_hash():
+        return None
+    return float(t.group(1))
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"sped_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.25)
+        return self
+
+    def __exit__(self, *a):
+        time.sleep(0.2)
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if hasattr(self, "f"):
+            self.f.close()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        try:
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                         "sw_power_cap"]
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        except OSError:
+            pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------------------
+def _principal_angle(sped, Vstar, V, k):
+    """Largest principal angle between span(V*) and span(V) from their FP64 Gram."""
+    G = sped.gram(Vstar, k, V, k).cpu().numpy()
+    Ps, C, Pv = G[:k, :k], G[:k, k:], G[k:, k:]
+    Rs = np.linalg.cholesky(Ps)
+    Rv = np.linalg.cholesky(Pv)
+    M = np.linalg.solve(Rs, np.linalg.solve(Rv, C.T).T)  # Q*^T Q_V
+    smin = np.linalg.svd(M, compute_uv=False).min()
+    return float(math.asin(math.sqrt(max(0.0, 1.0 - min(1.0, smin) ** 2))))
+
+
+def time_to_bottom_k(sped, torch, G, V0, k, stream, lam_bound, max_plain=4000):
+    """Two passes per arm: an instrumented run finds the first step whose angle to the
+    reference subspace is <= 1e-3, then a timed run executes exactly that many steps."""
+    dev = V0.device
+    n = V0.shape[0]
+    # reference subspace: FP64 subspace iteration on the dilated operator, run far past the
+    # tolerance (contraction ~0.06 per step at this gap), with its invariant-subspace residual
+    G.set_polynomial(sped.POLY_LIMIT_EXP, WORKLOAD["ell"])
+    Vs = sped.alloc_block(n, k, torch.float64, dev)
+    Vs[:, :k] = V0[:, :k].double()
+    ref_opts = sped.step_opts(sped.OJA, 0.0, torch.float64, torch.float64)
+    stats = torch.zeros(3 * k, dtype=torch.float64, device=dev)
+    scr = torch.empty(sped.eig_step_scratch_bytes(G, ref_opts, k), dtype=torch.uint8, device=dev)
+    for _ in range(14):
+        sped.eig_step(G, Vs, k, ref_opts, stats=stats, scratch=scr)
+    torch.cuda.synchronize()
+    ref_residual = float(stats[k:2 * k].max())
+    del scr
+
+    arms = {
+        "dilated_mixed_mu_eg": dict(poly=("limit", 7), solver=sped.MU_EG, eta=1.5,
+                                    chain=torch.bfloat16, master=torch.float32, cap=400),
+        "dilated_mixed_oja": dict(poly=("limit", 15), solver=sped.OJA, eta=0.0,
+                                  chain=torch.bfloat16, master=torch.float32, cap=200),
+        "plain_fp64_mu_eg": dict(poly=("shift", 1), solver=sped.MU_EG, eta=None,
+                                 chain=torch.float64, master=torch.float64, cap=max_plain),
+        "plain_fp32_mu_eg": dict(poly=("shift", 1), solver=sped.MU_EG, eta=None,
+                                 chain=torch.float32, master=torch.float32, cap=max_plain),
+    }
+    out = {"reference": {"solver": "oja_fp64_limit", "degree": WORKLOAD["ell"], "steps": 14,
+                         "invariant_subspace_residual": ref_residual}}
+    for name, a in arms.items():
+        if a["poly"][0] == "limit":
+            info = G.set_polynomial(sped.POLY_LIMIT_EXP, a["poly"][1])
+        else:
+            info = G.set_polynomial(sped.POLY_SHIFT, 1)
+        eta = a["eta"] if a["eta"] is not None else 2.0 / info.lambda_star
+        y_t = torch.float32 if a["master"] == torch.float32 else torch.float64
+        opts = sped.step_opts(a["solver"], eta, a["chain"], y_t)
+        scr = torch.empty(sped.eig_step_scratch_bytes(G, opts, k), dtype=torch.uint8, device=dev)
+        V = sped.alloc_block(n, k, a["master"], dev)
+        V[:, :k] = V0[:, :k].to(a["master"])
+        steps, ang = None, None
+        check = 1 if a["cap"] <= 400 else 5
+        for t in range(1, a["cap"] + 1):
+            sped.eig_step(G, V, k, opts, scratch=scr)
+            if t % check == 0 or t == a["cap"]:
+                ang = _principal_angle(sped, Vs, V, k)
+                if ang <= 1e-3:
+                    steps = t
+                    break
+        if steps is not None and check > 1:  # refine to the exact first step
+            V[:, :k] = V0[:, :k].to(a["master"])
+            for t in range(1, steps + 1):
+                sped.eig_step(G, V, k, opts, scratch=scr)
+                if t > steps - check:
+                    ang = _principal_angle(sped, Vs, V, k)
+                    if ang <= 1e-3:
+                        steps = t
+                        break
+        rec = {"steps": steps, "angle": ang, "degree": info.degree, "eta": eta,
+               "spmm": None if steps is None else steps * info.degree}
+        if steps is not None:
+            V[:, :k] = V0[:, :k].to(a["master"])
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                sped.eig_step(G, V, k, opts, scratch=scr)
+            e1.record(stream)
+            e1.synchronize()
+            rec["ms"] = e0.elapsed_time(e1)
+            rec["angle_after_timed_run"] = _principal_angle(sped, Vs, V, k)
+        out[name] = rec
+        del scr, V
+    d, p = out.get("dilated_mixed_mu_eg", {}), out.get("plain_fp64_mu_eg", {})
+    if d.get("ms") and p.get("ms"):
+        out["speedup_mu_eg_dilated_vs_plain"] = p["ms"] / d["ms"]
+    do = out.get("dilated_mixed_oja", {})
+    if do.get("ms") and p.get("ms"):
+        out["speedup_best_dilated_vs_plain"] = p["ms"] / min(d.get("ms") or 1e30, do["ms"])
+    G.set_polynomial(sped.POLY_LIMIT_EXP, WORKLOAD["ell"])
+    return out
+
+
+def cpu_baseline(g, sample_steps=None):
+    """The FP64 oracle (as it stands, one host thread) on a bounded sample of the same work:
+    a few chain steps X <- X - sL X on the full graph at k = 20."""
+    import oracle
+    k = WORKLOAD["k"]
+    V = gen.gaussian_block(g.n, k, seed=SEED)
+    s = 1.0 / WORKLOAD["ell"]
+    t0 = time.perf_counter()
+    oracle.poly_limit(g, V, s, 1)
+    one = time.perf_counter() - t0
+    m = sample_steps or max(1, min(40, int(12.0 / max(one, 1e-3))))
+    t0 = time.perf_counter()
+    oracle.poly_limit(g, V, s, m)
+    dt = time.perf_counter() - t0
+    b = m * spmm_bytes(g.n, g.nnz, k, 2, 2)
+    return {"value": b / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"{m} limit-form chain steps X <- X - sL X over the full graph, k={k}, "
+                      f"FP64, single host thread, {dt:.2f} s; bytes counted as one BF16 chain "
+                      f"step of the GPU arm"}
+
+
+# ----------------------------------------------------------------------------------------
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    g = make_graph()
+    cb = cpu_baseline(g)
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "GB/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": _config(g),
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": "GB/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def _config(g):
+    w = WORKLOAD
+    return {"workload": f"sbm_n{w['n']}_b{w['blocks']}_deg16_k{w['k']}",
+            "n": g.n, "nnz": g.nnz, "k": w["k"], "degree_l": w["ell"], "blocks": w["blocks"],
+            "p_in": w["p_in"], "p_out": w["p_out"], "seed": SEED,
+            "chain": "bf16 storage, f32 accumulate; f32 master V; f64 k x k",
+            "solver": "mu-EG, eta=1.0, limit form (I - sL)^l",
+            "l2": "working set (graph 68 MB + blocks >= 200 MB) larger than L2 (129 MB)"}
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_2207_14589_gb300 as sped
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    g = make_graph()
+    w = WORKLOAD
+    k, ell = w["k"], w["ell"]
+    G = sped.Graph.from_csr(g, device=dev)
+    info = G.set_polynomial(sped.POLY_LIMIT_EXP, ell)
+    V0 = torch.from_numpy(gen.gaussian_block(g.n, k, seed=SEED + rank)).to(dev)
+    V0 = V0 / V0.norm(dim=0)
+    V = sped.alloc_block(g.n, k, torch.float32, dev)
+    V[:, :k] = V0.float()
+    opts = sped.step_opts(sped.MU_EG, 1.0, torch.bfloat16, torch.float32)
+    scr = torch.empty(sped.eig_step_scratch_bytes(G, opts, k), dtype=torch.uint8, device=dev)
+    K, W = args.steps, args.warmup
+    for _ in range(W):
+        sped.eig_step(G, V, k, opts, scratch=scr)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(K)]
+    for b, e in ev:  # torch creates the underlying cudaEvent_t at the first record
+        b.record(stream)
+        e.record(stream)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local_rank if "CUDA_VISIBLE_DEVICES" not in os.environ else
+                os.environ["CUDA_VISIBLE_DEVICES"].split(",")[local_rank]) as clk:
+        t_start.record(stream)
+        for i in range(K):
+            opts.ev_chain_begin = ctypes_ptr(ev[i][0])
+            opts.ev_chain_end = ctypes_ptr(ev[i][1])
+            sped.eig_step(G, V, k, opts, scratch=scr)
+        t_end.record(stream)
+        t_end.synchronize()
+    torch.cuda.synchronize()
+    ms_total = t_start.elapsed_time(t_end)
+    opts.ev_chain_begin = None
+    opts.ev_chain_end = None
+    chain_ms = [b.elapsed_time(e) for b, e in ev]
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t)
+        dist.barrier()
+    chain_b, step_b = step_bytes(g.n, g.nnz, k, ell)
+    ms_step = ms_total / K
+    value = world * step_b / (ms_step * 1e-3) / 1e9
+    peak, peak_kind = _peaks()
+    mean_chain_ms = float(np.mean(chain_ms))
+    launch_ms = mean_chain_ms / ell
+    per_launch_bytes = chain_b / ell
+    achieved = per_launch_bytes / (launch_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": _ncu_traffic(),
+                "kernel": "k_step_rowgroup (chain step, bf16 storage, f32 accumulate)",
+                "per_launch_bytes": per_launch_bytes, "launch_us": launch_ms * 1e3,
+                "peak_kind": f"{peak_kind} (copy, burst)"}
+
+    # end to end through the C ABI with host buffers: pinned H2D of V, the step, D2H of V
+    e2e_steps = min(K, 50)
+    hostV = torch.empty_like(V, device="cpu").pin_memory()
+    hostV.copy_(V.cpu())
+    hostOut = torch.empty_like(hostV).pin_memory()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        V.copy_(hostV, non_blocking=True)
+        sped.eig_step(G, V, k, opts, scratch=scr)
+        hostOut.copy_(V, non_blocking=True)
+    e1.record(stream)
+    e1.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    vb = V.numel() * V.element_size()
+    e2e = {"value": world * step_b / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s",
+           "h2d_bytes_per_step": vb, "d2h_bytes_per_step": vb, "ms_per_step": e2e_ms}
+
+    extra = {}
+    if rank == 0 and not args.no_ttk:
+        extra["time_to_bottom_k"] = time_to_bottom_k(sped, torch, G, V0.double(), k, stream,
+                                                     info.lambda_bound)
+    clocks = clk.summary()
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": K,
+            "warmup": W, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic", "config": _config(g),
+            "roofline": roofline, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": K * (ell + 4),
+            "poly_gbs": chain_b / (mean_chain_ms * 1e-3) / 1e9,
+            "step_bytes": step_b}
+    line.update(extra)
+    if not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(g)
+    print(json.dumps(line), flush=True)
+
+
+def ctypes_ptr(event):
+    return event.cuda_event
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-ttk", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,273 @@
+/*
+ * sped.h -- C ABI of the GB300 (sm_103a) implementation of the hot path of
+ * "Stochastic Parallelizable Eigengap Dilation for Large Graph Clustering"
+ * (van der Pol, Gemp, Bachrach, Everett; arXiv 2207.14589).
+ *
+ * The hot path applies an eigenvector-preserving polynomial p(L) of a sparse graph Laplacian
+ * to an n x k block V (exactly by chained CSR SpMM, or by the paper's unbiased random-walk
+ * estimate) and feeds p(L) V into a bottom-k eigensolver step (mu-EigenGame or Oja).
+ *
+ * Conventions for every entry point
+ *  - Pointers named d_* are CUDA device pointers on the current device; h_* are host pointers.
+ *    The caller owns every buffer. Nothing on the per-step path allocates: scratch memory is
+ *    passed in, sized by the matching *_scratch_size query. Scratch must be 256-byte aligned.
+ *  - Dense blocks are row-major n x k with leading dimension ld (elements, ld >= k). The vector
+ *    path needs ld * sizeof(element) to be a multiple of 16 bytes and 16-byte aligned bases;
+ *    other layouts are rejected with SPED_ERR_INVALID_ARG.
+ *  - stream is a cudaStream_t passed as void* (NULL = legacy default stream). Work is
+ *    stream-ordered; entry points return after enqueueing unless documented as synchronising.
+ *  - Arguments are validated on the host before any launch; a rejected call launches nothing.
+ *    Errors found on the device (invalid CSR, non-positive-definite Gram, a bounded wait that
+ *    gave up) are reported by the next synchronising call. sped_last_error() returns a
+ *    thread-local message for the last failing call on this thread.
+ *  - Graph input: symmetric adjacency in CSR with int32 row_ptr[n+1] and col_idx[nnz],
+ *    columns strictly increasing within each row, no self loops; optional float32 weights per
+ *    stored entry, equal for (i,j) and (j,i).
+ */
+#ifndef SPED_H
+#define SPED_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sped_graph sped_graph; /* opaque: device metadata of one graph */
+
+typedef enum {
+    SPED_OK = 0,
+    SPED_ERR_INVALID_ARG = 1,   /* bad pointer, size, layout or option */
+    SPED_ERR_BAD_CSR = 2,       /* graph violates the input convention above */
+    SPED_ERR_UNSUPPORTED = 3,   /* valid request with no kernel (e.g. dtype combination) */
+    SPED_ERR_NUMERIC = 4,       /* NaN/Inf, or a Gram that is not positive definite */
+    SPED_ERR_NOT_CONVERGED = 5, /* solver stopped at max_steps above tolerance */
+    SPED_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up */
+    SPED_ERR_CUDA = 7,          /* CUDA runtime error (message in sped_last_error) */
+    SPED_ERR_SCRATCH = 8        /* scratch buffer too small or misaligned */
+} sped_status;
+
+typedef enum { SPED_BF16 = 0, SPED_F32 = 1, SPED_F64 = 2 } sped_dtype;
+
+/* Polynomial families (Table 2 of the paper; reversal of Eq. reveig folded in so that the
+ * wanted bottom-k eigenvectors of L are the top-k of the operator M that is applied). */
+typedef enum {
+    SPED_POLY_LIMIT_EXP = 0,  /* M = (I - sL)^l, l odd: reversed limit form -(I - L/l)^l   */
+    SPED_POLY_TAYLOR_EXP = 1, /* M = sum_{i<=l} (-L)^i / i!: reversed Taylor -e^{-L}        */
+    SPED_POLY_TAYLOR_LOG = 2, /* M = lambda* I - sum_{i=1}^{l} (-1)^{i+1} (L+(eps-1)I)^i / i */
+    SPED_POLY_MONOMIAL = 3,   /* M = sum_i c_i L^i with caller coefficients c_0..c_l        */
+    SPED_POLY_SHIFT = 4       /* M = lambda* I - L: the plain reversed Laplacian, Eq. reveig */
+} sped_poly_kind;
+
+typedef enum {
+    SPED_EXACT = 0,            /* chained SpMM                                           */
+    SPED_STOCHASTIC_IS = 1,    /* random-walk estimate, importance weights (Section 4.3) */
+    SPED_STOCHASTIC_REJECT = 2 /* random-walk estimate, the text's rejection step        */
+} sped_mode;
+
+typedef enum { SPED_SOLVER_MU_EG = 0, SPED_SOLVER_OJA = 1 } sped_solver;
+
+/* ------------------------------------------------------------------------------------
+ * Graph set-up (Section 2: L = D - A; end of Section 2.1: weighted L = X^T W X).
+ * ------------------------------------------------------------------------------------ */
+
+/* Bytes of device workspace sped_build_laplacian needs for a graph with n nodes and nnz
+ * stored entries (reverse-entry map, undirected edge ids, edge list, weight copy). */
+sped_status sped_workspace_size(int64_t n, int64_t nnz, size_t *bytes);
+
+/* Validate the CSR (when check != 0), derive the reverse-entry map, the undirected edge list
+ * (edges numbered by the CSR order of their upper entries a < b), weighted degrees and the
+ * spectral bound lambda_max <= 2 max_i d_i (Section 5.4). row_ptr/col_idx (and d_w when not
+ * NULL) must stay valid while the graph is used; d_workspace holds the derived arrays.
+ * Synchronises the stream. On success *out receives a graph handle; the default polynomial
+ * is SPED_POLY_SHIFT with lambda* = the spectral bound. */
+sped_status sped_build_laplacian(int64_t n, int64_t nnz, const int32_t *d_row_ptr,
+                                 const int32_t *d_col_idx, const float *d_w, void *d_workspace,
+                                 size_t ws_bytes, int check, void *stream, sped_graph **out);
+
+void sped_graph_destroy(sped_graph *g);
+
+typedef struct {
+    int64_t n, nnz, n_edges;
+    int32_t max_degree;     /* largest neighbour count deg* (Section 4.3)              */
+    double max_wdegree;     /* largest weighted degree                                 */
+    double lambda_bound;    /* 2 * max weighted degree >= lambda_max                    */
+    int weighted;
+    /* resolved polynomial */
+    int poly_kind, degree;
+    double scale_s, shift, lambda_star;
+} sped_graph_info;
+
+sped_status sped_graph_get_info(const sped_graph *g, sped_graph_info *info);
+
+/* Device arrays of the undirected edge list: d_edge_a[e] < d_edge_b[e], e in [0, n_edges).
+ * Either output may be NULL. */
+sped_status sped_graph_edges(const sped_graph *g, int32_t *d_edge_a, int32_t *d_edge_b,
+                             void *stream);
+
+/* Replace the weights by one float32 per undirected edge (edge order as above), e.g. learned
+ * weights. Writes the per-entry copy kept in the workspace; the graph uses it from then on.
+ * Synchronises (the spectral bound is recomputed). */
+sped_status sped_set_edge_weights(sped_graph *g, const float *d_w_edge, void *stream);
+
+/* ------------------------------------------------------------------------------------
+ * Polynomial (Sections 4.1-4.2, Table 2).
+ *  degree     l >= 1 (odd required for SPED_POLY_LIMIT_EXP so the map is monotone on R).
+ *  scale_s    limit form only; 0 = automatic: 1/l when l >= lambda_bound/2, else
+ *             2/lambda_bound, so that |1 - s lambda| <= 1 on the whole spectrum.
+ *  eps        Taylor log only (the table's eps << 1); 0 = 1e-3.
+ *  coeffs     SPED_POLY_MONOMIAL only: l+1 host doubles c_0..c_l.
+ *  lambda_star SHIFT and TAYLOR_LOG: 0 = automatic (the spectral bound, or for the log the
+ *             series' value bound).
+ * ------------------------------------------------------------------------------------ */
+sped_status sped_set_polynomial(sped_graph *g, sped_poly_kind kind, int degree, double scale_s,
+                                double eps, const double *coeffs, double lambda_star);
+
+/* Power-basis coefficients c_0..c_l of the operator M = sum_i c_i L^i (h_out: l+1 doubles). */
+sped_status sped_get_power_coeffs(const sped_graph *g, double *h_out, int capacity);
+
+/* ------------------------------------------------------------------------------------
+ * One fused step of the polynomial chain (the hot kernel):
+ *   Y[r,:] = alpha V[r,:] + gamma X[r,:] + beta (d_r X[r,:] - sum_j w_rj X[j,:])
+ * i.e. Y = alpha V + gamma X + beta L X. d_V may be NULL when alpha == 0. X and Y must not
+ * overlap. Supported (x, y) storage pairs: (F64,F64) (F32,F32) (BF16,BF16) (F32,BF16)
+ * (BF16,F32) (F32,F64); accumulation in F64 when y is F64, else F32. V (when used) is
+ * F32 or F64, or BF16 when x is BF16.
+ * split: 0 = automatic, 1 = row-group kernel, 2 = merge-path kernel (needs scratch).
+ * ------------------------------------------------------------------------------------ */
+sped_status sped_poly_step(const sped_graph *g, int k, const void *d_X, sped_dtype x_t, int ldx,
+                           const void *d_V, sped_dtype v_t, int ldv, void *d_Y, sped_dtype y_t,
+                           int ldy, double alpha, double beta, double gamma, int split,
+                           void *d_scratch, size_t scratch_bytes, void *stream);
+
+sped_status sped_poly_step_scratch_size(const sped_graph *g, int k, sped_dtype x_t, int split,
+                                        size_t *bytes);
+
+/* ------------------------------------------------------------------------------------
+ * Y = M V for the graph's polynomial M (Sections 4.2-4.3).
+ *  mode SPED_EXACT: the chain of poly steps; intermediate products stored as chain_t
+ *    (BF16 halves gather traffic, accumulation stays F32), the last step writes y_t.
+ *  mode SPED_STOCHASTIC_*: Y = c_0 V + mean over `walkers` walks of the sampled terms
+ *    (Section 4.3), draws from Philox4x32-10 keyed by seed (documented in walk.cu);
+ *    y_t must be F32 or F64; chain_t is ignored.
+ * ------------------------------------------------------------------------------------ */
+sped_status sped_apply_poly(const sped_graph *g, int k, const void *d_V, sped_dtype v_t, int ldv,
+                            void *d_Y, sped_dtype y_t, int ldy, sped_dtype chain_t,
+                            sped_mode mode, int64_t walkers, uint64_t seed, void *d_scratch,
+                            size_t scratch_bytes, void *stream);
+
+sped_status sped_apply_poly_scratch_size(const sped_graph *g, int k, sped_dtype chain_t,
+                                         sped_mode mode, size_t *bytes);
+
+/* ------------------------------------------------------------------------------------
+ * Gram of a tall-skinny pair: G = [A B]^T [A B], (ka+kb) x (ka+kb) row-major FP64,
+ * ka + kb <= 64. d_B may be NULL (kb = 0). Products in F32 for BF16/F32 inputs (exact for
+ * BF16), accumulated in F32 over short row tiles and in F64 across tiles and CTAs;
+ * F64 inputs use F64 throughout. Deterministic (fixed reduction order).
+ * ------------------------------------------------------------------------------------ */
+sped_status sped_gram(int64_t n, const void *d_A, sped_dtype a_t, int lda, int ka, const void *d_B,
+                      sped_dtype b_t, int ldb, int kb, double *d_G, void *d_scratch,
+                      size_t scratch_bytes, void *stream);
+
+sped_status sped_gram_scratch_size(int64_t n, int ka, int kb, size_t *bytes);
+
+/* ------------------------------------------------------------------------------------
+ * One solver step on the graph's operator M (Section 5.1: mu-EG and Oja; Section 3 for the
+ * reversal). V (n x k, F32 or F64 master copy, k <= 32) is updated in place:
+ *  mu-EG: delta_i = y_i - sum_{j<i} <v_i,y_j> v_j, r_i = delta_i - <v_i,delta_i> v_i,
+ *         v_i <- (v_i + eta r_i)/||.||, all inner products from the Gram [V Y]^T [V Y];
+ *  Oja:   V <- (V + eta Y) R^{-1} with R the Cholesky factor of its Gram (eta <= 0: V <- Y R^{-1}).
+ * d_stats (device, 3k doubles, may be NULL): Rayleigh quotients <v_i,Mv_i>/<v_i,v_i>; the
+ * invariant-subspace residuals ||(I - P_V) y_i|| / ||y_i|| (P_V the orthogonal projector onto
+ * span(V) before the step; zero exactly when span(V) is M-invariant); the step sizes
+ * ||v_i(new) - v_i||.
+ * ------------------------------------------------------------------------------------ */
+typedef struct {
+    sped_solver solver;
+    double eta;
+    sped_dtype chain_t; /* storage of intermediate products                           */
+    sped_dtype y_t;     /* storage of Y = M V: F32 or F64                              */
+    sped_mode mode;     /* exact or stochastic p(L) V                                  */
+    int64_t walkers;
+    uint64_t seed;
+    /* optional cudaEvent_t pair (as void*, NULL = none) recorded on the stream immediately
+     * before and after the p(L) V chain, for live timing of the dominant kernel */
+    void *ev_chain_begin;
+    void *ev_chain_end;
+} sped_step_opts;
+
+sped_status sped_eig_step(const sped_graph *g, const sped_step_opts *opts, void *d_V,
+                          sped_dtype v_t, int k, int ld, double *d_stats, void *d_scratch,
+                          size_t scratch_bytes, void *stream);
+
+sped_status sped_eig_step_scratch_size(const sped_graph *g, const sped_step_opts *opts, int k,
+                                       size_t *bytes);
+
+/* Rayleigh quotients of the Laplacian itself, lambda_i = <v_i, L v_i>/<v_i, v_i>, in FP64
+ * (d_out: k doubles). */
+sped_status sped_rayleigh(const sped_graph *g, const void *d_V, sped_dtype v_t, int k, int ld,
+                          double *d_out, void *d_scratch, size_t scratch_bytes, void *stream);
+
+sped_status sped_rayleigh_scratch_size(const sped_graph *g, int k, size_t *bytes);
+
+/* ------------------------------------------------------------------------------------
+ * Iterate eig_step to convergence (synchronising). The convergence measure is the largest
+ * invariant-subspace residual max_i ||(I - P_V) y_i|| / ||y_i|| (second block of d_stats), which
+ * tracks the sine of the angle between span(V) and span(MV). Phase 1 stores the chain in
+ * opts.step.chain_t (e.g. BF16) until the measure is <= switch_tol or phase1_steps steps;
+ * phase 2 uses refine_chain_t (e.g. F32) until <= tol. The test reads the statistics every
+ * check_every steps. h_lambda (host, k doubles, may be NULL) receives the
+ * Rayleigh quotients of L.
+ * ------------------------------------------------------------------------------------ */
+typedef struct {
+    sped_step_opts step;
+    int max_steps;
+    int check_every;
+    double tol;
+    double switch_tol;
+    int phase1_steps;
+    sped_dtype refine_chain_t;
+} sped_solve_opts;
+
+typedef struct {
+    int steps;
+    int phase1_steps;
+    int64_t spmm_count;
+    double final_residual; /* largest invariant-subspace residual at exit */
+    int converged;
+} sped_solve_report;
+
+sped_status sped_solve_bottom_k(const sped_graph *g, const sped_solve_opts *opts, void *d_V,
+                                sped_dtype v_t, int k, int ld, double *h_lambda,
+                                sped_solve_report *report, void *d_scratch, size_t scratch_bytes,
+                                void *stream);
+
+sped_status sped_solve_scratch_size(const sped_graph *g, const sped_solve_opts *opts, int k,
+                                    size_t *bytes);
+
+/* ------------------------------------------------------------------------------------
+ * Hard clustering (Sections 1 and 2.1): k-means on the rows of V (n x k, any dtype), rows not
+ * normalised. k-means++ seeding from Philox4x32-10 (key = seed; centre 0 is a bounded draw
+ * from the word stream of counter (0, 0, 0x6B6D, j), centre c >= 1 uses u = (w + 0.5) 2^-32
+ * with w the first word of counter (c, 0, 0, 0x6B6D), taking the first row whose running sum
+ * of squared distances exceeds u times the total); Lloyd iterations in FP64 until labels stop
+ * changing or max_iter; ties to the lowest centroid; an empty cluster restarts at the
+ * farthest point; labels renumbered by first occurrence. Synchronises; *h_iters (may be
+ * NULL) receives the Lloyd iteration count.
+ * ------------------------------------------------------------------------------------ */
+sped_status sped_cluster_assign(const void *d_V, sped_dtype v_t, int64_t n, int k, int ld,
+                                int n_clusters, uint64_t seed, int max_iter, int32_t *d_labels,
+                                int *h_iters, void *d_scratch, size_t scratch_bytes, void *stream);
+
+sped_status sped_cluster_scratch_size(int64_t n, int k, int n_clusters, size_t *bytes);
+
+/* ------------------------------------------------------------------------------------ */
+const char *sped_last_error(void);
+const char *sped_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPED_H */

@@ -1,0 +1,293 @@
+// Internal declarations shared by the CUDA translation units of libsped (not part of the ABI).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <vector>
+
+#include "../../include/sped.h"
+
+namespace sped {
+
+// ---------------------------------------------------------------------------------------
+// host-side error reporting
+// ---------------------------------------------------------------------------------------
+void set_error(const char *fmt, ...);
+sped_status fail(sped_status st, const char *fmt, ...);
+sped_status cuda_fail(cudaError_t e, const char *where);
+
+#define SPED_CUDA(expr)                                                        \
+    do {                                                                       \
+        cudaError_t _e = (expr);                                               \
+        if (_e != cudaSuccess) return ::sped::cuda_fail(_e, #expr);            \
+    } while (0)
+
+#define SPED_CHECK_LAUNCH(name)                                                \
+    do {                                                                       \
+        cudaError_t _e = cudaGetLastError();                                   \
+        if (_e != cudaSuccess) return ::sped::cuda_fail(_e, name);             \
+    } while (0)
+
+#define SPED_TRY(expr)                                                         \
+    do {                                                                       \
+        sped_status _s = (expr);                                               \
+        if (_s != SPED_OK) return _s;                                          \
+    } while (0)
+
+inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+inline size_t dtype_size(sped_dtype t) {
+    return t == SPED_BF16 ? 2 : (t == SPED_F32 ? 4 : 8);
+}
+inline bool dtype_valid(int t) { return t == SPED_BF16 || t == SPED_F32 || t == SPED_F64; }
+
+// elements per 16-byte chunk
+inline int chunk_elems(sped_dtype t) { return (int)(16 / dtype_size(t)); }
+
+// leading dimension rounded so that a row is a whole number of 16-byte chunks
+inline int padded_ld(int k, sped_dtype t) {
+    int e = chunk_elems(t);
+    return (k + e - 1) / e * e;
+}
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Simple bump allocator over a caller-provided scratch buffer (256-byte aligned pieces).
+struct Scratch {
+    char *base;
+    size_t cap, used;
+    Scratch(void *p, size_t bytes) : base((char *)p), cap(bytes), used(0) {}
+    void *take(size_t bytes) {
+        size_t off = align_up(used, 256);
+        if (off + bytes > cap || (base == nullptr && bytes > 0)) return nullptr;
+        used = off + bytes;
+        return base + off;
+    }
+};
+
+// size accounting twin of Scratch
+struct ScratchPlan {
+    size_t used = 0;
+    void add(size_t bytes) { used = align_up(used, 256) + bytes; }
+    size_t total() const { return align_up(used, 256); }
+};
+
+int device_sm_count();
+
+// ---------------------------------------------------------------------------------------
+// graph
+// ---------------------------------------------------------------------------------------
+struct Poly {
+    int kind = SPED_POLY_SHIFT;
+    int ell = 1;
+    double s = 0.0;            // limit form scale
+    double shift = 0.0;        // Horner: T = L + shift I
+    double lambda_star = 0.0;  // SHIFT / LOG reversal
+    double eps = 0.0;
+    std::vector<double> horner;  // c_0..c_l in powers of T (Horner kinds)
+    std::vector<double> power;   // c_0..c_l in powers of L (stochastic mode)
+};
+
+}  // namespace sped
+
+struct sped_graph {
+    int device;
+    int64_t n, nnz, n_edges;
+    const int32_t *rp, *ci;
+    const float *w;       // active per-entry weights (caller array or ws_w) or nullptr
+    int32_t *rev;         // rev[p]: position of the reverse entry of p
+    int32_t *eid;         // undirected edge id of entry p
+    int32_t *edge_p;      // entry position (row a, col b, a < b) of edge e
+    int32_t *edge_a;      // row a of edge e
+    int32_t *eoff;        // first edge id of row r (n+1)
+    float *ws_w;          // workspace copy for weights set per edge
+    void *stats;          // small device statistics slot inside the workspace
+    int32_t max_deg;
+    double max_wdeg;
+    double lambda_bound;
+    sped::Poly poly;
+};
+
+namespace sped {
+
+// ---------------------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------------------
+template <typename T> struct AccOf { using type = float; };
+template <> struct AccOf<double> { using type = double; };
+
+// Element conversion to an accumulator type A (float or double) and back.
+template <typename A> __device__ __forceinline__ A cvt(__nv_bfloat16 x);
+template <> __device__ __forceinline__ float cvt<float>(__nv_bfloat16 x) { return __bfloat162float(x); }
+template <> __device__ __forceinline__ double cvt<double>(__nv_bfloat16 x) {
+    return (double)__bfloat162float(x);
+}
+template <typename A> __device__ __forceinline__ A cvt(float x) { return (A)x; }
+template <typename A> __device__ __forceinline__ A cvt(double x) { return (A)x; }
+
+template <typename T> __device__ __forceinline__ T from_acc(float x);
+template <typename T> __device__ __forceinline__ T from_acc(double x);
+template <> __device__ __forceinline__ float from_acc<float>(float x) { return x; }
+template <> __device__ __forceinline__ float from_acc<float>(double x) { return (float)x; }
+template <> __device__ __forceinline__ double from_acc<double>(float x) { return (double)x; }
+template <> __device__ __forceinline__ double from_acc<double>(double x) { return x; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_acc<__nv_bfloat16>(float x) {
+    return __float2bfloat16_rn(x);
+}
+template <> __device__ __forceinline__ __nv_bfloat16 from_acc<__nv_bfloat16>(double x) {
+    return __float2bfloat16_rn((float)x);
+}
+
+template <int BYTES> struct VecOf;
+template <> struct VecOf<4> { using type = uint32_t; };
+template <> struct VecOf<8> { using type = uint2; };
+template <> struct VecOf<16> { using type = uint4; };
+
+// Read E consecutive elements (E * sizeof(T) bytes, naturally aligned) through the read-only
+// path, converting to the accumulator type.
+template <typename T, int E, typename A>
+__device__ __forceinline__ void load_chunk(const T *__restrict__ p, A (&out)[E]) {
+    constexpr int BYTES = E * (int)sizeof(T);
+    static_assert(BYTES == 4 || BYTES == 8 || BYTES == 16 || BYTES == 32 || BYTES == 64, "chunk");
+    constexpr int VB = BYTES < 16 ? BYTES : 16;
+    constexpr int NV = BYTES / VB;
+    constexpr int PER = VB / (int)sizeof(T);
+    using V = typename VecOf<VB>::type;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        union { V v; T e[PER]; } u;
+        u.v = __ldg(reinterpret_cast<const V *>(p) + q);
+#pragma unroll
+        for (int i = 0; i < PER; ++i) out[q * PER + i] = cvt<A>(u.e[i]);
+    }
+}
+
+// Plain (coherent) load of a chunk, for data written earlier in the same kernel.
+template <typename T, int E, typename A>
+__device__ __forceinline__ void load_chunk_coherent(const T *p, A (&out)[E]) {
+    constexpr int BYTES = E * (int)sizeof(T);
+    constexpr int VB = BYTES < 16 ? BYTES : 16;
+    constexpr int NV = BYTES / VB;
+    constexpr int PER = VB / (int)sizeof(T);
+    using V = typename VecOf<VB>::type;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        union { V v; T e[PER]; } u;
+        u.v = reinterpret_cast<const V *>(p)[q];
+#pragma unroll
+        for (int i = 0; i < PER; ++i) out[q * PER + i] = cvt<A>(u.e[i]);
+    }
+}
+
+template <typename T, int E, typename A>
+__device__ __forceinline__ void store_chunk(T *p, const A (&in)[E]) {
+    constexpr int BYTES = E * (int)sizeof(T);
+    constexpr int VB = BYTES < 16 ? BYTES : 16;
+    constexpr int NV = BYTES / VB;
+    constexpr int PER = VB / (int)sizeof(T);
+    using V = typename VecOf<VB>::type;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        union { V v; T e[PER]; } u;
+#pragma unroll
+        for (int i = 0; i < PER; ++i) u.e[i] = from_acc<T>(in[q * PER + i]);
+        reinterpret_cast<V *>(p)[q] = u.v;
+    }
+}
+
+// Tail-safe versions: only the first `cnt` (< E) elements are touched.
+template <typename T, int E, typename A>
+__device__ __forceinline__ void load_partial(const T *__restrict__ p, int cnt, A (&out)[E]) {
+#pragma unroll
+    for (int i = 0; i < E; ++i) out[i] = i < cnt ? cvt<A>(p[i]) : A(0);
+}
+template <typename T, int E, typename A>
+__device__ __forceinline__ void store_partial(T *p, int cnt, const A (&in)[E]) {
+#pragma unroll
+    for (int i = 0; i < E; ++i)
+        if (i < cnt) p[i] = from_acc<T>(in[i]);
+}
+
+// Philox4x32-10 (Salmon et al., SC'11) -- device implementation of the published definition.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k.x += W0;
+            k.y += W1;
+        }
+        uint32_t hi0 = __umulhi(M0, c.x), lo0 = M0 * c.x;
+        uint32_t hi1 = __umulhi(M1, c.z), lo1 = M1 * c.z;
+        uint4 n;
+        n.x = hi1 ^ c.y ^ k.x;
+        n.y = lo1;
+        n.z = hi0 ^ c.w ^ k.y;
+        n.w = lo0;
+        c = n;
+    }
+    return c;
+}
+
+// Word stream: words of philox(key, {a, b, tag, j}) for j = 0, 1, 2, ... in order.
+struct WordStream {
+    uint2 key;
+    uint32_t a, b, tag, j;
+    uint4 buf;
+    int used;
+    __device__ __forceinline__ WordStream(uint64_t seed, uint32_t a_, uint32_t b_, uint32_t tag_)
+        : a(a_), b(b_), tag(tag_), j(0), used(4) {
+        key.x = (uint32_t)seed;
+        key.y = (uint32_t)(seed >> 32);
+    }
+    __device__ __forceinline__ uint32_t next() {
+        if (used == 4) {
+            buf = philox4x32_10(make_uint4(a, b, tag, j), key);
+            ++j;
+            used = 0;
+        }
+        uint32_t r = used == 0 ? buf.x : used == 1 ? buf.y : used == 2 ? buf.z : buf.w;
+        ++used;
+        return r;
+    }
+    // Lemire's multiply-and-reject bounded draw in [0, range), range >= 1.
+    __device__ __forceinline__ uint32_t bounded(uint32_t range) {
+        uint32_t x = next();
+        uint64_t m = (uint64_t)x * range;
+        uint32_t l = (uint32_t)m;
+        if (l < range) {
+            uint32_t t = (uint32_t)(0u - range) % range;
+            while (l < t) {
+                x = next();
+                m = (uint64_t)x * range;
+                l = (uint32_t)m;
+            }
+        }
+        return (uint32_t)(m >> 32);
+    }
+};
+
+// Internal launchers shared across translation units.
+sped_status launch_poly_step(const sped_graph *g, int k, const void *X, sped_dtype xt, int ldx,
+                             const void *V, sped_dtype vt, int ldv, void *Y, sped_dtype yt, int ldy,
+                             double alpha, double beta, double gamma, int split, Scratch &scr,
+                             cudaStream_t st);
+size_t poly_step_scratch(const sped_graph *g, int k, sped_dtype xt, int split);
+sped_status launch_gram(int64_t n, const void *A, sped_dtype at, int lda, int ka, const void *B,
+                        sped_dtype bt, int ldb, int kb, double *G, Scratch &scr, cudaStream_t st);
+size_t gram_scratch(int64_t n, int ka, int kb);
+sped_status apply_poly_impl(const sped_graph *g, int k, const void *V, sped_dtype vt, int ldv,
+                            void *Y, sped_dtype yt, int ldy, sped_dtype ct, sped_mode mode,
+                            int64_t walkers, uint64_t seed, Scratch &scr, cudaStream_t st);
+size_t apply_poly_scratch(const sped_graph *g, int k, sped_dtype ct, sped_mode mode);
+sped_status launch_walk(const sped_graph *g, int k, const void *V, sped_dtype vt, int ldv, void *Y,
+                        sped_dtype yt, int ldy, sped_mode mode, int64_t walkers, uint64_t seed,
+                        cudaStream_t st);
+sped_status check_layout(const void *p, sped_dtype t, int k, int ld, const char *name);
+
+}  // namespace sped

@@ -1,0 +1,548 @@
+// The hot kernel: one fused step of the polynomial chain,
+//     Y = alpha V + gamma X + beta L X,   L = D - A  (Section 2; weighted: end of Section 2.1)
+// chained by apply_poly into the limit form (I - sL)^l (Table 2, last row; alpha=0, gamma=1,
+// beta=-s), Horner's rule for the Taylor rows of Table 2 (alpha=c_j, beta=1, gamma=shift), or
+// the plain reversed Laplacian lambda* I - L of Eq. reveig (gamma=lambda*, beta=-1).
+//
+// Two schedules, same arithmetic:
+//  * row-group: C = ceil(k * sizeof(Tx) / 16) lanes share one row, each owning one 16-byte
+//    chunk of the row vector across all neighbours (no cross-lane reduction); 32/C rows per
+//    warp; four neighbours in flight per lane. Degree d_r is summed in the same loop.
+//  * merge-path: equal shares of (rows + nonzeros) per lane group (Merrill & Garland's merge
+//    path over row ends and nonzeros) for skewed degree distributions; rows cut by a share
+//    boundary leave partial sums in scratch, finished by a fix-up kernel in fixed order.
+#include "sped_internal.cuh"
+
+namespace sped {
+
+constexpr int STEP_THREADS = 256;
+constexpr int UNROLL = 4;
+
+template <typename Tx, typename Tv, typename Ty, typename A, bool W, bool HV>
+struct StepArgs {
+    int n;
+    const int32_t *__restrict__ rp;
+    const int32_t *__restrict__ ci;
+    const float *__restrict__ w;
+    const Tx *__restrict__ X;
+    int ldx;
+    const Tv *__restrict__ V;
+    int ldv;
+    Ty *__restrict__ Y;
+    int ldy;
+    int k;
+    int C;
+    A alpha, beta, gamma;
+};
+
+// epilogue of row r for the lane's chunk: out = alpha v + gamma x + beta (d x - acc)
+template <typename Tx, typename Tv, typename Ty, typename A, bool W, bool HV, int E>
+__device__ __forceinline__ void finish_row(const StepArgs<Tx, Tv, Ty, A, W, HV> &a, int64_t r,
+                                           int c, const A (&acc)[E], A dsum) {
+    A xr[E];
+    load_chunk<Tx, E, A>(a.X + r * a.ldx + c * E, xr);
+    A out[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) out[i] = a.gamma * xr[i] + a.beta * (dsum * xr[i] - acc[i]);
+    const int rem = a.k - c * E;
+    if constexpr (HV) {
+        A vr[E];
+        if (rem >= E) load_chunk<Tv, E, A>(a.V + r * a.ldv + c * E, vr);
+        else load_partial<Tv, E, A>(a.V + r * a.ldv + c * E, rem, vr);
+#pragma unroll
+        for (int i = 0; i < E; ++i) out[i] += a.alpha * vr[i];
+    }
+    if (rem >= E) store_chunk<Ty, E, A>(a.Y + r * a.ldy + c * E, out);
+    else store_partial<Ty, E, A>(a.Y + r * a.ldy + c * E, rem, out);
+}
+
+// accumulate neighbours [p, p1) of the lane's chunk into acc / dsum
+template <typename Tx, typename Tv, typename Ty, typename A, bool W, bool HV, int E>
+__device__ __forceinline__ void gather_range(const StepArgs<Tx, Tv, Ty, A, W, HV> &a, int c, int p,
+                                             int p1, A (&acc)[E], A &dsum) {
+    const Tx *Xc = a.X + c * E;
+    for (; p + UNROLL <= p1; p += UNROLL) {
+        int j[UNROLL];
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) j[u] = __ldg(a.ci + p + u);
+        A x[UNROLL][E];
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) load_chunk<Tx, E, A>(Xc + (int64_t)j[u] * a.ldx, x[u]);
+        if constexpr (W) {
+            A wv[UNROLL];
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u) wv[u] = (A)__ldg(a.w + p + u);
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u) {
+                dsum += wv[u];
+#pragma unroll
+                for (int i = 0; i < E; ++i) acc[i] += wv[u] * x[u][i];
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u)
+#pragma unroll
+                for (int i = 0; i < E; ++i) acc[i] += x[u][i];
+        }
+    }
+    for (; p < p1; ++p) {
+        int j = __ldg(a.ci + p);
+        A x[E];
+        load_chunk<Tx, E, A>(Xc + (int64_t)j * a.ldx, x);
+        if constexpr (W) {
+            A wv = (A)__ldg(a.w + p);
+            dsum += wv;
+#pragma unroll
+            for (int i = 0; i < E; ++i) acc[i] += wv * x[i];
+        } else {
+#pragma unroll
+            for (int i = 0; i < E; ++i) acc[i] += x[i];
+        }
+    }
+}
+
+template <typename Tx, typename Tv, typename Ty, typename A, bool W, bool HV>
+__global__ void __launch_bounds__(STEP_THREADS)
+k_step_rowgroup(StepArgs<Tx, Tv, Ty, A, W, HV> a, int rows_per_warp) {
+    constexpr int E = 16 / (int)sizeof(Tx);
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * STEP_THREADS + threadIdx.x) >> 5;
+    const int rw = lane / a.C;
+    const int c = lane - rw * a.C;
+    if (rw >= rows_per_warp) return;
+    const int64_t r = warp * rows_per_warp + rw;
+    if (r >= a.n) return;
+    const int p0 = __ldg(a.rp + r), p1 = __ldg(a.rp + r + 1);
+    A acc[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) acc[i] = A(0);
+    A dsum = A(0);
+    gather_range<Tx, Tv, Ty, A, W, HV, E>(a, c, p0, p1, acc, dsum);
+    if constexpr (!W) dsum = (A)(p1 - p0);
+    finish_row<Tx, Tv, Ty, A, W, HV, E>(a, r, c, acc, dsum);
+}
+
+// ---------------------------------------------------------------------------------------
+// merge path
+// ---------------------------------------------------------------------------------------
+// first (row, nonzero) coordinate of merge-path diagonal `diag`: the number of row ends i and
+// nonzeros j consumed, i + j = diag, row end i consumed once j >= rp[i+1].
+__device__ __forceinline__ void merge_search(int64_t diag, int n, int nnz,
+                                             const int32_t *__restrict__ rp, int &i, int &j) {
+    int64_t lo = diag > nnz ? diag - nnz : 0;
+    int64_t hi = diag < n ? diag : n;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if ((int64_t)__ldg(rp + mid + 1) <= diag - mid - 1) lo = mid + 1;
+        else hi = mid;
+    }
+    i = (int)lo;
+    j = (int)(diag - lo);
+}
+
+template <typename A> struct MergeParts {
+    A *acc;        // [groups][2][KP]  (0 = head, 1 = tail)
+    A *dsum;       // [groups][2]
+    int32_t *row;  // [groups][2]      (-1 = none)
+    int KP;
+};
+
+template <typename Tx, typename Tv, typename Ty, typename A, bool W, bool HV>
+__global__ void __launch_bounds__(STEP_THREADS)
+k_step_merge(StepArgs<Tx, Tv, Ty, A, W, HV> a, int nnz, int groups_per_warp, int64_t ipg,
+             int64_t n_groups, MergeParts<A> parts) {
+    constexpr int E = 16 / (int)sizeof(Tx);
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * STEP_THREADS + threadIdx.x) >> 5;
+    const int gw = lane / a.C;
+    const int c = lane - gw * a.C;
+    if (gw >= groups_per_warp) return;
+    const int64_t g = warp * groups_per_warp + gw;
+    if (g >= n_groups) return;
+    const int64_t total = (int64_t)a.n + nnz;
+    const int64_t d0 = g * ipg;
+    const int64_t d1 = d0 + ipg < total ? d0 + ipg : total;
+    int i0, j0, i1, j1;
+    merge_search(d0, a.n, nnz, a.rp, i0, j0);
+    merge_search(d1, a.n, nnz, a.rp, i1, j1);
+    const Tx *Xc = a.X + c * E;
+    A acc[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) acc[i] = A(0);
+    A dsum = A(0);
+    int i = i0;
+    int rstart = (i0 < a.n) ? __ldg(a.rp + i0) : nnz;  // first nonzero of row i
+    int rnext = (i0 < a.n) ? __ldg(a.rp + i0 + 1) : nnz;
+    int64_t hslot = g * 2;
+    if (c == 0) {
+        parts.row[hslot] = -1;
+        parts.row[hslot + 1] = -1;
+    }
+    auto end_row = [&]() {
+        A ds = dsum;
+        if constexpr (!W) ds = (A)(rnext - (rstart > j0 ? rstart : j0));
+        if (i > i0 || rstart >= j0) {
+            if constexpr (!W) ds = (A)(rnext - rstart);
+            finish_row<Tx, Tv, Ty, A, W, HV, E>(a, i, c, acc, ds);
+        } else {  // row began in an earlier share: leave the head piece for the fix-up
+#pragma unroll
+            for (int q = 0; q < E; ++q) parts.acc[hslot * parts.KP + c * E + q] = acc[q];
+            if (c == 0) {
+                parts.dsum[hslot] = ds;
+                parts.row[hslot] = i;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < E; ++q) acc[q] = A(0);
+        dsum = A(0);
+        ++i;
+        rstart = rnext;
+        rnext = (i < a.n) ? __ldg(a.rp + i + 1) : nnz;
+    };
+    int p = j0;
+    for (; p + UNROLL <= j1; p += UNROLL) {
+        int jj[UNROLL];
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) jj[u] = __ldg(a.ci + p + u);
+        A x[UNROLL][E];
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) load_chunk<Tx, E, A>(Xc + (int64_t)jj[u] * a.ldx, x[u]);
+        A wv[UNROLL];
+        if constexpr (W) {
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u) wv[u] = (A)__ldg(a.w + p + u);
+        }
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) {
+            while (p + u >= rnext && i < i1) end_row();
+            if constexpr (W) {
+                dsum += wv[u];
+#pragma unroll
+                for (int q = 0; q < E; ++q) acc[q] += wv[u] * x[u][q];
+            } else {
+#pragma unroll
+                for (int q = 0; q < E; ++q) acc[q] += x[u][q];
+            }
+        }
+    }
+    for (; p < j1; ++p) {
+        while (p >= rnext && i < i1) end_row();
+        int jx = __ldg(a.ci + p);
+        A x[E];
+        load_chunk<Tx, E, A>(Xc + (int64_t)jx * a.ldx, x);
+        if constexpr (W) {
+            A wv = (A)__ldg(a.w + p);
+            dsum += wv;
+#pragma unroll
+            for (int q = 0; q < E; ++q) acc[q] += wv * x[q];
+        } else {
+#pragma unroll
+            for (int q = 0; q < E; ++q) acc[q] += x[q];
+        }
+    }
+    while (i < i1) end_row();
+    if (i1 < a.n) {  // unfinished last row: tail piece
+        A ds = dsum;
+        if constexpr (!W) ds = (A)(j1 - (rstart > j0 ? rstart : j0));
+#pragma unroll
+        for (int q = 0; q < E; ++q) parts.acc[(hslot + 1) * parts.KP + c * E + q] = acc[q];
+        if (c == 0) {
+            parts.dsum[hslot + 1] = ds;
+            parts.row[hslot + 1] = i1;
+        }
+    }
+}
+
+// Finish rows cut by share boundaries: the share holding a row's end sums its head piece and
+// the tail pieces of the preceding shares (walking back while they belong to the row).
+template <typename Tx, typename Tv, typename Ty, typename A, bool W, bool HV>
+__global__ void __launch_bounds__(STEP_THREADS)
+k_merge_fixup(StepArgs<Tx, Tv, Ty, A, W, HV> a, int groups_per_warp, int64_t n_groups,
+              MergeParts<A> parts) {
+    constexpr int E = 16 / (int)sizeof(Tx);
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * STEP_THREADS + threadIdx.x) >> 5;
+    const int gw = lane / a.C;
+    const int c = lane - gw * a.C;
+    if (gw >= groups_per_warp) return;
+    const int64_t g = warp * groups_per_warp + gw;
+    if (g >= n_groups) return;
+    const int r = parts.row[g * 2];
+    if (r < 0) return;
+    A acc[E];
+    A dsum = parts.dsum[g * 2];
+#pragma unroll
+    for (int q = 0; q < E; ++q) acc[q] = parts.acc[(g * 2) * parts.KP + c * E + q];
+    for (int64_t h = g - 1; h >= 0 && parts.row[h * 2 + 1] == r; --h) {
+        dsum += parts.dsum[h * 2 + 1];
+#pragma unroll
+        for (int q = 0; q < E; ++q) acc[q] += parts.acc[(h * 2 + 1) * parts.KP + c * E + q];
+    }
+    finish_row<Tx, Tv, Ty, A, W, HV, E>(a, r, c, acc, dsum);
+}
+
+// ---------------------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------------------
+static bool use_merge(const sped_graph *g, int split) {
+    if (split == 1) return false;
+    if (split == 2) return true;
+    double avg = g->n ? (double)g->nnz / (double)g->n : 0.0;
+    return g->max_deg > 128 && g->max_deg > 8.0 * avg;
+}
+
+struct MergePlan {
+    int64_t ipg, n_groups;
+    int KP;
+    size_t acc_bytes, dsum_bytes, row_bytes;
+};
+
+static MergePlan merge_plan(const sped_graph *g, int k, sped_dtype xt, size_t acc_size) {
+    MergePlan m;
+    int E = chunk_elems(xt);
+    int C = (k + E - 1) / E;
+    int64_t total = g->n + g->nnz;
+    int64_t lanes = (int64_t)device_sm_count() * 2048;
+    int64_t target_groups = lanes / C * 2;
+    int64_t ipg = (total + target_groups - 1) / (target_groups > 0 ? target_groups : 1);
+    if (ipg < 32) ipg = 32;
+    m.ipg = ipg;
+    m.n_groups = (total + ipg - 1) / ipg;
+    m.KP = C * E;
+    m.acc_bytes = (size_t)m.n_groups * 2 * m.KP * acc_size;
+    m.dsum_bytes = (size_t)m.n_groups * 2 * acc_size;
+    m.row_bytes = (size_t)m.n_groups * 2 * sizeof(int32_t);
+    return m;
+}
+
+static size_t acc_size_for(sped_dtype yt) { return yt == SPED_F64 ? 8 : 4; }
+
+size_t poly_step_scratch(const sped_graph *g, int k, sped_dtype xt, int split) {
+    if (!use_merge(g, split)) return 0;
+    MergePlan m = merge_plan(g, k, xt, 8);
+    ScratchPlan p;
+    p.add(m.acc_bytes);
+    p.add(m.dsum_bytes);
+    p.add(m.row_bytes);
+    return p.total();
+}
+
+template <typename Tx, typename Tv, typename Ty, typename A, bool W, bool HV>
+static sped_status run_step(const sped_graph *g, int k, const void *X, int ldx, const void *V,
+                            int ldv, void *Y, int ldy, double alpha, double beta, double gamma,
+                            int split, Scratch &scr, cudaStream_t st) {
+    constexpr int E = 16 / (int)sizeof(Tx);
+    StepArgs<Tx, Tv, Ty, A, W, HV> a;
+    a.n = (int)g->n;
+    a.rp = g->rp;
+    a.ci = g->ci;
+    a.w = g->w;
+    a.X = (const Tx *)X;
+    a.ldx = ldx;
+    a.V = (const Tv *)V;
+    a.ldv = ldv;
+    a.Y = (Ty *)Y;
+    a.ldy = ldy;
+    a.k = k;
+    a.C = (k + E - 1) / E;
+    a.alpha = (A)alpha;
+    a.beta = (A)beta;
+    a.gamma = (A)gamma;
+    if (a.C > 32) return fail(SPED_ERR_UNSUPPORTED, "poly_step: row of %d chunks > 32", a.C);
+    const int per_warp = 32 / a.C;
+    if (!use_merge(g, split)) {
+        int64_t warps = (g->n + per_warp - 1) / per_warp;
+        int64_t blocks = (warps * 32 + STEP_THREADS - 1) / STEP_THREADS;
+        if (blocks > 0) k_step_rowgroup<Tx, Tv, Ty, A, W, HV><<<(unsigned)blocks, STEP_THREADS, 0, st>>>(a, per_warp);
+        SPED_CHECK_LAUNCH("k_step_rowgroup");
+        return SPED_OK;
+    }
+    MergePlan m = merge_plan(g, k, sizeof(Tx) == 2 ? SPED_BF16 : sizeof(Tx) == 4 ? SPED_F32 : SPED_F64,
+                             sizeof(A));
+    MergeParts<A> parts;
+    parts.acc = (A *)scr.take(m.acc_bytes);
+    parts.dsum = (A *)scr.take(m.dsum_bytes);
+    parts.row = (int32_t *)scr.take(m.row_bytes);
+    parts.KP = m.KP;
+    if (!parts.acc || !parts.dsum || !parts.row)
+        return fail(SPED_ERR_SCRATCH, "poly_step (merge path): scratch too small");
+    int64_t warps = (m.n_groups + per_warp - 1) / per_warp;
+    int64_t blocks = (warps * 32 + STEP_THREADS - 1) / STEP_THREADS;
+    k_step_merge<Tx, Tv, Ty, A, W, HV><<<(unsigned)blocks, STEP_THREADS, 0, st>>>(
+        a, (int)g->nnz, per_warp, m.ipg, m.n_groups, parts);
+    SPED_CHECK_LAUNCH("k_step_merge");
+    k_merge_fixup<Tx, Tv, Ty, A, W, HV><<<(unsigned)blocks, STEP_THREADS, 0, st>>>(
+        a, per_warp, m.n_groups, parts);
+    SPED_CHECK_LAUNCH("k_merge_fixup");
+    return SPED_OK;
+}
+
+template <typename Tx, typename Tv, typename Ty, typename A, bool HV>
+static sped_status run_step_w(const sped_graph *g, int k, const void *X, int ldx, const void *V,
+                              int ldv, void *Y, int ldy, double al, double be, double ga, int split,
+                              Scratch &scr, cudaStream_t st) {
+    if (g->w)
+        return run_step<Tx, Tv, Ty, A, true, HV>(g, k, X, ldx, V, ldv, Y, ldy, al, be, ga, split,
+                                                 scr, st);
+    return run_step<Tx, Tv, Ty, A, false, HV>(g, k, X, ldx, V, ldv, Y, ldy, al, be, ga, split,
+                                              scr, st);
+}
+
+using bf16 = __nv_bfloat16;
+
+sped_status launch_poly_step(const sped_graph *g, int k, const void *X, sped_dtype xt, int ldx,
+                             const void *V, sped_dtype vt, int ldv, void *Y, sped_dtype yt,
+                             int ldy, double al, double be, double ga, int split, Scratch &scr,
+                             cudaStream_t st) {
+    const bool hv = V != nullptr && al != 0.0;
+#define STEP(TX, TV, TY, ACC, HVV)                                                            \
+    return run_step_w<TX, TV, TY, ACC, HVV>(g, k, X, ldx, V, ldv, Y, ldy, al, be, ga, split,   \
+                                            scr, st)
+    if (!hv) {
+        if (xt == SPED_F64 && yt == SPED_F64) STEP(double, double, double, double, false);
+        if (xt == SPED_F32 && yt == SPED_F32) STEP(float, float, float, float, false);
+        if (xt == SPED_BF16 && yt == SPED_BF16) STEP(bf16, bf16, bf16, float, false);
+        if (xt == SPED_F32 && yt == SPED_BF16) STEP(float, float, bf16, float, false);
+        if (xt == SPED_BF16 && yt == SPED_F32) STEP(bf16, bf16, float, float, false);
+        if (xt == SPED_F32 && yt == SPED_F64) STEP(float, float, double, double, false);
+    } else {
+        if (xt == SPED_F64 && yt == SPED_F64 && vt == SPED_F64) STEP(double, double, double, double, true);
+        if (xt == SPED_F64 && yt == SPED_F64 && vt == SPED_F32) STEP(double, float, double, double, true);
+        if (xt == SPED_F32 && yt == SPED_F32 && vt == SPED_F32) STEP(float, float, float, float, true);
+        if (xt == SPED_BF16 && yt == SPED_BF16 && vt == SPED_F32) STEP(bf16, float, bf16, float, true);
+        if (xt == SPED_F32 && yt == SPED_BF16 && vt == SPED_F32) STEP(float, float, bf16, float, true);
+        if (xt == SPED_BF16 && yt == SPED_F32 && vt == SPED_F32) STEP(bf16, float, float, float, true);
+        if (xt == SPED_F32 && yt == SPED_F64 && vt == SPED_F32) STEP(float, float, double, double, true);
+        if (xt == SPED_F32 && yt == SPED_F64 && vt == SPED_F64) STEP(float, double, double, double, true);
+    }
+#undef STEP
+    return fail(SPED_ERR_UNSUPPORTED, "poly_step: unsupported dtype combination x=%d y=%d v=%d",
+                (int)xt, (int)yt, hv ? (int)vt : -1);
+}
+
+// ---------------------------------------------------------------------------------------
+// exact p(L) V: the chain of steps for the graph's polynomial
+// ---------------------------------------------------------------------------------------
+struct StepCoef {
+    double alpha, beta, gamma;
+    bool uses_v;
+};
+
+static std::vector<StepCoef> chain_coefs(const Poly &P) {
+    std::vector<StepCoef> out;
+    if (P.kind == SPED_POLY_LIMIT_EXP) {
+        for (int t = 0; t < P.ell; ++t) out.push_back({0.0, -P.s, 1.0, false});
+    } else if (P.kind == SPED_POLY_SHIFT) {
+        out.push_back({0.0, -1.0, P.lambda_star, false});
+    } else {
+        const auto &h = P.horner;
+        const int l = P.ell;
+        // Z_{l-1} = h_{l-1} V + T (h_l V) = (h_{l-1} + h_l shift) V + h_l L V
+        out.push_back({0.0, h[l], h[l - 1] + h[l] * P.shift, false});
+        for (int j = l - 2; j >= 0; --j) out.push_back({h[j], 1.0, P.shift, true});
+    }
+    return out;
+}
+
+size_t apply_poly_scratch(const sped_graph *g, int k, sped_dtype ct, sped_mode mode) {
+    if (mode != SPED_EXACT) return 0;
+    int steps = (int)chain_coefs(g->poly).size();
+    ScratchPlan p;
+    size_t buf = (size_t)g->n * padded_ld(k, ct) * dtype_size(ct);
+    if (steps >= 2) p.add(buf);
+    if (steps >= 3) p.add(buf);
+    size_t ms = 0;
+    for (sped_dtype t : {SPED_BF16, SPED_F32, SPED_F64}) {
+        size_t x = poly_step_scratch(g, k, t, 0);
+        if (x > ms) ms = x;
+    }
+    p.add(ms);
+    return p.total();
+}
+
+sped_status apply_poly_impl(const sped_graph *g, int k, const void *V, sped_dtype vt, int ldv,
+                            void *Y, sped_dtype yt, int ldy, sped_dtype ct, sped_mode mode,
+                            int64_t walkers, uint64_t seed, Scratch &scr, cudaStream_t st) {
+    if (mode != SPED_EXACT)
+        return launch_walk(g, k, V, vt, ldv, Y, yt, ldy, mode, walkers, seed, st);
+    std::vector<StepCoef> cs = chain_coefs(g->poly);
+    const int steps = (int)cs.size();
+    const int ldc = padded_ld(k, ct);
+    const size_t buf = (size_t)g->n * ldc * dtype_size(ct);
+    void *b[2] = {nullptr, nullptr};
+    if (steps >= 2) b[0] = scr.take(buf);
+    if (steps >= 3) b[1] = scr.take(buf);
+    if ((steps >= 2 && !b[0]) || (steps >= 3 && !b[1]))
+        return fail(SPED_ERR_SCRATCH, "apply_poly: scratch too small for the chain buffers");
+    // what is left of the caller's scratch after the chain buffers serves each step in turn
+    const size_t off = align_up(scr.used, 256);
+    const size_t rest = (scr.base != nullptr && off < scr.cap) ? scr.cap - off : 0;
+    Scratch step_scr(rest ? scr.base + off : nullptr, rest);
+    for (int t = 0; t < steps; ++t) {
+        const void *x = t == 0 ? V : b[(t - 1) % 2];
+        sped_dtype xt = t == 0 ? vt : ct;
+        int ldx = t == 0 ? ldv : ldc;
+        void *y = t == steps - 1 ? Y : b[t % 2];
+        sped_dtype ytt = t == steps - 1 ? yt : ct;
+        int ldyy = t == steps - 1 ? ldy : ldc;
+        step_scr.used = 0;
+        SPED_TRY(launch_poly_step(g, k, x, xt, ldx, cs[t].uses_v ? V : nullptr, vt, ldv, y, ytt,
+                                  ldyy, cs[t].alpha, cs[t].beta, cs[t].gamma, 0, step_scr, st));
+    }
+    return SPED_OK;
+}
+
+}  // namespace sped
+
+using namespace sped;
+
+extern "C" {
+
+sped_status sped_poly_step_scratch_size(const sped_graph *g, int k, sped_dtype x_t, int split,
+                                        size_t *bytes) {
+    if (!g || !bytes || k < 1 || !dtype_valid(x_t))
+        return fail(SPED_ERR_INVALID_ARG, "poly_step_scratch_size: bad args");
+    *bytes = poly_step_scratch(g, k, x_t, split);
+    return SPED_OK;
+}
+
+sped_status sped_poly_step(const sped_graph *g, int k, const void *d_X, sped_dtype x_t, int ldx,
+                           const void *d_V, sped_dtype v_t, int ldv, void *d_Y, sped_dtype y_t,
+                           int ldy, double alpha, double beta, double gamma, int split,
+                           void *d_scratch, size_t scratch_bytes, void *stream) {
+    if (!g) return fail(SPED_ERR_INVALID_ARG, "poly_step: null graph");
+    if (split < 0 || split > 2) return fail(SPED_ERR_INVALID_ARG, "poly_step: split %d", split);
+    SPED_TRY(check_layout(d_X, x_t, k, ldx, "poly_step X"));
+    SPED_TRY(check_layout(d_Y, y_t, k, ldy, "poly_step Y"));
+    if (d_V && alpha != 0.0) SPED_TRY(check_layout(d_V, v_t, k, ldv, "poly_step V"));
+    if (d_X == d_Y) return fail(SPED_ERR_INVALID_ARG, "poly_step: X and Y must not alias");
+    Scratch scr(d_scratch, scratch_bytes);
+    return launch_poly_step(g, k, d_X, x_t, ldx, d_V, v_t, ldv, d_Y, y_t, ldy, alpha, beta, gamma,
+                            split, scr, as_stream(stream));
+}
+
+sped_status sped_apply_poly_scratch_size(const sped_graph *g, int k, sped_dtype chain_t,
+                                         sped_mode mode, size_t *bytes) {
+    if (!g || !bytes || k < 1 || !dtype_valid(chain_t))
+        return fail(SPED_ERR_INVALID_ARG, "apply_poly_scratch_size: bad args");
+    *bytes = apply_poly_scratch(g, k, chain_t, mode);
+    return SPED_OK;
+}
+
+sped_status sped_apply_poly(const sped_graph *g, int k, const void *d_V, sped_dtype v_t, int ldv,
+                            void *d_Y, sped_dtype y_t, int ldy, sped_dtype chain_t, sped_mode mode,
+                            int64_t walkers, uint64_t seed, void *d_scratch, size_t scratch_bytes,
+                            void *stream) {
+    if (!g) return fail(SPED_ERR_INVALID_ARG, "apply_poly: null graph");
+    SPED_TRY(check_layout(d_V, v_t, k, ldv, "apply_poly V"));
+    SPED_TRY(check_layout(d_Y, y_t, k, ldy, "apply_poly Y"));
+    if (!dtype_valid(chain_t)) return fail(SPED_ERR_INVALID_ARG, "apply_poly: chain dtype");
+    if (mode != SPED_EXACT && mode != SPED_STOCHASTIC_IS && mode != SPED_STOCHASTIC_REJECT)
+        return fail(SPED_ERR_INVALID_ARG, "apply_poly: mode %d", (int)mode);
+    if (d_V == d_Y) return fail(SPED_ERR_INVALID_ARG, "apply_poly: V and Y must not alias");
+    Scratch scr(d_scratch, scratch_bytes);
+    return apply_poly_impl(g, k, d_V, v_t, ldv, d_Y, y_t, ldy, chain_t, mode, walkers, seed, scr,
+                           as_stream(stream));
+}
+
+}  // extern "C"

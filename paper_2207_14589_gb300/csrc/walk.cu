@@ -1,0 +1,183 @@
+// Stochastic estimate of p(L) V over sampled walks (Section 4.3), one thread per walker.
+//
+// Eq. walk_summand writes L^i as a sum over chains e_1..e_i of the edge-incidence graph (a self
+// loop on every node, footnote of Section 4.3) of alpha_c x~_{e1} x~_{ei}^T, alpha_c the product
+// of consecutive incidence inner products (Table 1, scaled by sqrt(w_e w_f) for weights).
+// Each walker draws e_1 uniformly from the |E| undirected edges, then walks l-1 steps, each
+// uniform over the deg(a)+deg(b)-1 edges incident to the current edge {a,b} (itself included).
+// One walk serves every term i <= l (linearity of expectation, Section 4.3). The walker keeps
+// sum_i c_i w_i alpha_i (V[a_i] - V[b_i]) in registers and scatters it once into rows a_1 and
+// b_1 of Y (atomics), so a walk costs two row atomics instead of two per term.
+//  * importance weights: w_i = 1/q_i = |E| prod_{t<i} deg_inc(e_t);
+//  * rejection (as in the text): prefix i is kept with probability p_min,i / q_i,
+//    p_min,i = |E|^{-1} (2 deg* - 1)^{-(i-1)}, and then weighted 1/p_min,i.
+//
+// Random draws (the same published specification the reference implements separately):
+// Philox4x32-10 with key (seed_lo, seed_hi); walker w, step tag t: words of
+// philox(key, {w_lo, w_hi, t, j}), j = 0, 1, ..., bounded draws by Lemire's multiply-and-reject;
+// t = 0 draws e_1 in [0, |E|), t = i (1 <= i < l) draws the step after term i; the acceptance
+// uniform of prefix i is (word + 0.5) 2^-32 of the first word of tag 0x80000000 | i.
+// Edge ids follow the CSR order of the upper entries (a < b); the step rule takes a's r-th
+// neighbour for r < deg(a), else b's (r - deg(a))-th neighbour with a skipped.
+#include <cmath>
+
+#include "sped_internal.cuh"
+
+namespace sped {
+
+constexpr int WALK_MAX_ELL = 511;
+constexpr int WALK_THREADS = 128;
+
+struct WalkCoefs {
+    double c[WALK_MAX_ELL + 1];
+};
+
+__device__ __forceinline__ double inc_dot(int a1, int b1, double w1, int a2, int b2, double w2) {
+    // both edges already ordered (a < b); signs: +1 at the smaller node, -1 at the larger
+    double d = 0.0;
+    if (a1 == a2) d += 1.0;
+    if (a1 == b2) d -= 1.0;
+    if (b1 == a2) d -= 1.0;
+    if (b1 == b2) d += 1.0;
+    return sqrt(w1) * sqrt(w2) * d;
+}
+
+template <typename Ty, typename Tv>
+__global__ void k_walk_init(int64_t n, int k, const Tv *__restrict__ V, int ldv, double c0,
+                            Ty *__restrict__ Y, int ldy) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * k) return;
+    int64_t r = e / k;
+    int j = (int)(e - r * k);
+    Y[r * ldy + j] = from_acc<Ty>(c0 * cvt<double>(V[r * ldv + j]));
+}
+
+template <typename Tv, typename Ty, bool W, int KM>
+__global__ void __launch_bounds__(WALK_THREADS)
+k_walk(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const float *__restrict__ w,
+       const int32_t *__restrict__ rev, const int32_t *__restrict__ edge_p,
+       const int32_t *__restrict__ edge_a, int64_t n_edges, const Tv *__restrict__ V, int ldv,
+       int k, int ell, int64_t walkers, uint64_t seed, int mode, double dstar_inc, WalkCoefs cf,
+       Ty *__restrict__ Y, int ldy) {
+    const double inv_m = 1.0 / (double)walkers;
+    for (int64_t wk = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; wk < walkers;
+         wk += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t wlo = (uint32_t)wk, whi = (uint32_t)((uint64_t)wk >> 32);
+        WordStream s0(seed, wlo, whi, 0u);
+        const int e1 = (int)s0.bounded((uint32_t)n_edges);
+        int pc = __ldg(edge_p + e1);
+        const int a1 = __ldg(edge_a + e1), b1 = __ldg(ci + pc);
+        const double w1 = W ? (double)__ldg(w + pc) : 1.0;
+        int a = a1, b = b1;
+        double wc = w1;
+        double alpha = 1.0, inv_q = (double)n_edges, accept = 1.0;
+        double acc[KM];
+#pragma unroll
+        for (int j = 0; j < KM; ++j) acc[j] = 0.0;
+        for (int i = 1; i <= ell; ++i) {
+            double scale;
+            if (mode == SPED_STOCHASTIC_IS) {
+                scale = cf.c[i] * alpha * inv_q * sqrt(w1) * sqrt(wc);
+            } else {
+                WordStream su(seed, wlo, whi, 0x80000000u | (uint32_t)i);
+                double u = ((double)su.next() + 0.5) * (1.0 / 4294967296.0);
+                double inv_pmin = (double)n_edges * pow(dstar_inc, (double)(i - 1));
+                scale = (u < accept) ? cf.c[i] * alpha * inv_pmin * sqrt(w1) * sqrt(wc) : 0.0;
+            }
+            if (scale != 0.0) {
+                const Tv *va = V + (int64_t)a * ldv, *vb = V + (int64_t)b * ldv;
+#pragma unroll
+                for (int j = 0; j < KM; ++j)
+                    if (j < k) acc[j] += scale * (cvt<double>(va[j]) - cvt<double>(vb[j]));
+            }
+            if (i == ell) break;
+            const int ra = __ldg(rp + a), da = __ldg(rp + a + 1) - ra;
+            const int rb = __ldg(rp + b), db = __ldg(rp + b + 1) - rb;
+            const int deg_inc = da + db - 1;
+            WordStream st(seed, wlo, whi, (uint32_t)i);
+            const int r = (int)st.bounded((uint32_t)deg_inc);
+            int q, na, nb;
+            if (r < da) {
+                q = ra + r;
+                na = a;
+            } else {
+                const int rr = r - da;
+                const int skip = __ldg(rev + pc) - rb;  // position of a in b's row
+                q = rb + rr + (rr >= skip ? 1 : 0);
+                na = b;
+            }
+            nb = __ldg(ci + q);
+            const int lo = na < nb ? na : nb, hi = na < nb ? nb : na;
+            const int pos = na < nb ? q : __ldg(rev + q);  // entry (lo, hi) in row lo
+            const double wn = W ? (double)__ldg(w + pos) : 1.0;
+            alpha *= inc_dot(a, b, wc, lo, hi, wn);
+            inv_q *= (double)deg_inc;
+            accept *= (double)deg_inc / dstar_inc;
+            a = lo;
+            b = hi;
+            pc = pos;
+            wc = wn;
+        }
+        Ty *ya = Y + (int64_t)a1 * ldy, *yb = Y + (int64_t)b1 * ldy;
+#pragma unroll
+        for (int j = 0; j < KM; ++j) {
+            if (j < k && acc[j] != 0.0) {
+                atomicAdd(ya + j, (Ty)(acc[j] * inv_m));
+                atomicAdd(yb + j, (Ty)(-acc[j] * inv_m));
+            }
+        }
+    }
+}
+
+template <typename Tv, typename Ty>
+static sped_status run_walk(const sped_graph *g, int k, const void *V, int ldv, void *Y, int ldy,
+                            sped_mode mode, int64_t walkers, uint64_t seed, cudaStream_t st) {
+    const Poly &P = g->poly;
+    const int ell = P.ell;
+    int64_t nk = g->n * (int64_t)k;
+    k_walk_init<Ty, Tv><<<(unsigned)((nk + 255) / 256), 256, 0, st>>>(
+        g->n, k, (const Tv *)V, ldv, P.power[0], (Ty *)Y, ldy);
+    SPED_CHECK_LAUNCH("k_walk_init");
+    if (g->n_edges == 0 || walkers == 0) return SPED_OK;
+    WalkCoefs cf;
+    for (int i = 0; i <= WALK_MAX_ELL; ++i) cf.c[i] = i <= ell ? P.power[i] : 0.0;
+    double dstar_inc = 2.0 * g->max_deg - 1.0;
+    int64_t blocks = (walkers + WALK_THREADS - 1) / WALK_THREADS;
+    int64_t cap = (int64_t)device_sm_count() * 16;
+    if (blocks > cap) blocks = cap;
+#define WALK(KMV)                                                                              \
+    do {                                                                                       \
+        if (g->w)                                                                              \
+            k_walk<Tv, Ty, true, KMV><<<(unsigned)blocks, WALK_THREADS, 0, st>>>(              \
+                g->rp, g->ci, g->w, g->rev, g->edge_p, g->edge_a, g->n_edges, (const Tv *)V,   \
+                ldv, k, ell, walkers, seed, (int)mode, dstar_inc, cf, (Ty *)Y, ldy);           \
+        else                                                                                   \
+            k_walk<Tv, Ty, false, KMV><<<(unsigned)blocks, WALK_THREADS, 0, st>>>(             \
+                g->rp, g->ci, g->w, g->rev, g->edge_p, g->edge_a, g->n_edges, (const Tv *)V,   \
+                ldv, k, ell, walkers, seed, (int)mode, dstar_inc, cf, (Ty *)Y, ldy);           \
+    } while (0)
+    if (k <= 8) WALK(8);
+    else if (k <= 16) WALK(16);
+    else WALK(32);
+#undef WALK
+    SPED_CHECK_LAUNCH("k_walk");
+    return SPED_OK;
+}
+
+sped_status launch_walk(const sped_graph *g, int k, const void *V, sped_dtype vt, int ldv, void *Y,
+                        sped_dtype yt, int ldy, sped_mode mode, int64_t walkers, uint64_t seed,
+                        cudaStream_t st) {
+    if (walkers < 0) return fail(SPED_ERR_INVALID_ARG, "walk: walkers < 0");
+    if (k > 32) return fail(SPED_ERR_UNSUPPORTED, "walk: k=%d > 32", k);
+    if (g->poly.ell > WALK_MAX_ELL)
+        return fail(SPED_ERR_UNSUPPORTED, "walk: degree %d > %d", g->poly.ell, WALK_MAX_ELL);
+    if (g->n_edges >= (int64_t)UINT32_MAX) return fail(SPED_ERR_UNSUPPORTED, "walk: too many edges");
+    if (yt == SPED_F32 && vt == SPED_F32) return run_walk<float, float>(g, k, V, ldv, Y, ldy, mode, walkers, seed, st);
+    if (yt == SPED_F64 && vt == SPED_F64) return run_walk<double, double>(g, k, V, ldv, Y, ldy, mode, walkers, seed, st);
+    if (yt == SPED_F64 && vt == SPED_F32) return run_walk<float, double>(g, k, V, ldv, Y, ldy, mode, walkers, seed, st);
+    if (yt == SPED_F32 && vt == SPED_BF16) return run_walk<__nv_bfloat16, float>(g, k, V, ldv, Y, ldy, mode, walkers, seed, st);
+    return fail(SPED_ERR_UNSUPPORTED, "walk: V dtype %d / Y dtype %d (Y must be F32 or F64)",
+                (int)vt, (int)yt);
+}
+
+}  // namespace sped

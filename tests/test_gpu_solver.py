@@ -1,0 +1,175 @@
+"""Parity of the Gram, the solver step (mu-EG / Oja, Section 5.1), the bottom-k solve and the
+hard clustering (Sections 1, 2.1) against the FP64 oracle, through the C ABI."""
+import numpy as np
+import pytest
+import torch
+
+import gen
+import oracle
+import paper_2207_14589_gb300 as sped
+from util_gpu import DEV, host, rel, stored, to_block
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("at,bt,tol", [(torch.float64, torch.float64, 1e-13),
+                                       (torch.float32, torch.float32, 2e-6),
+                                       (torch.bfloat16, torch.bfloat16, 1e-6),
+                                       (torch.float32, torch.float64, 1e-13)])
+@pytest.mark.parametrize("n,ka,kb", [(1, 1, 0), (1000, 4, 4), (33333, 20, 20), (5000, 32, 32),
+                                     (777, 7, 3)])
+def test_gram(at, bt, tol, n, ka, kb):
+    A0 = gen.gaussian_block(n, ka, seed=1)
+    B0 = gen.gaussian_block(n, kb, seed=2) if kb else None
+    A = to_block(A0, at)
+    B = to_block(B0, bt) if kb else None
+    G = sped.gram(A, ka, B, kb)
+    torch.cuda.synchronize()
+    M = stored(A0, at) if not kb else np.concatenate([stored(A0, at), stored(B0, bt)], axis=1)
+    want = M.T @ M
+    got = G.cpu().numpy()
+    assert np.array_equal(got, got.T)
+    assert rel(got, want) <= tol
+
+
+@pytest.mark.parametrize("solver", [sped.MU_EG, sped.OJA])
+@pytest.mark.parametrize("poly", ["limit", "shift"])
+def test_eig_step_fp64(solver, poly):
+    g = gen.sbm(1500, 3, 0.02, 0.001, seed=3)
+    G = sped.Graph.from_csr(g)
+    k = 5
+    if poly == "limit":
+        info = G.set_polynomial(sped.POLY_LIMIT_EXP, 9)
+    else:
+        info = G.set_polynomial(sped.POLY_SHIFT, 1)
+    V0 = gen.gaussian_block(g.n, k, seed=4)
+    V0 /= np.linalg.norm(V0, axis=0)
+    V = to_block(V0, torch.float64)
+    eta = 0.5 if solver == sped.MU_EG else 2.0
+    if poly == "shift":
+        eta /= info.lambda_star
+    opts = sped.step_opts(solver, eta, torch.float64, torch.float64)
+    stats = torch.zeros(3 * k, dtype=torch.float64, device=DEV)
+    sped.eig_step(G, V, k, opts, stats=stats)
+    torch.cuda.synchronize()
+    if poly == "limit":
+        Y0 = oracle.poly_limit(g, V0, info.scale_s, 9)
+    else:
+        Y0 = info.lambda_star * V0 - oracle.laplacian_apply(g, V0)
+    want = oracle.mu_eg_step(V0, Y0, eta) if solver == sped.MU_EG else oracle.oja_step(V0, Y0, eta)
+    assert np.abs(host(V, k) - want).max() <= 1e-10
+    st = stats.cpu().numpy()
+    assert np.allclose(st[:k], oracle.ritz_values(V0, Y0), rtol=1e-12)
+    # invariant-subspace residual ||(I - P_V) y_i|| / ||y_i|| and the step sizes
+    Q = oracle.orthonormal_basis(V0)
+    res = np.linalg.norm(Y0 - Q @ (Q.T @ Y0), axis=0) / np.linalg.norm(Y0, axis=0)
+    assert np.allclose(st[k:2 * k], res, rtol=1e-6, atol=1e-12)
+    assert np.allclose(st[2 * k:], np.linalg.norm(want - V0, axis=0), rtol=1e-7, atol=1e-12)
+
+
+def test_eig_step_mixed_precision_close_to_fp64():
+    g = gen.sbm(5000, 5, 0.01, 0.0004, seed=5)
+    G = sped.Graph.from_csr(g)
+    info = G.set_polynomial(sped.POLY_LIMIT_EXP, 21)
+    k = 5
+    V0 = gen.gaussian_block(g.n, k, seed=6)
+    V0 /= np.linalg.norm(V0, axis=0)
+    V = to_block(V0, torch.float32)
+    opts = sped.step_opts(sped.MU_EG, 1.0, torch.bfloat16, torch.float32)
+    sped.eig_step(G, V, k, opts)
+    torch.cuda.synchronize()
+    Vs = stored(V0, torch.float32)
+    want = oracle.mu_eg_step(Vs, oracle.poly_limit(g, Vs, info.scale_s, 21), 1.0)
+    assert rel(host(V, k), want) <= 1e-2
+
+
+def _config1():
+    return gen.sbm(2000, 4, 0.05, 0.001, seed=gen.DEFAULT_SEED)
+
+
+@pytest.mark.parametrize("arm", ["plain_fp64", "dilated_fp64", "dilated_mixed", "dilated_oja"])
+def test_solve_bottom_k_config1(arm):
+    g = _config1()
+    G = sped.Graph.from_csr(g)
+    k = 4
+    lam, Ustar = oracle.bottom_k(g, k)
+    V0 = gen.gaussian_block(g.n, k, seed=gen.DEFAULT_SEED)
+    if arm == "plain_fp64":
+        info = G.set_polynomial(sped.POLY_SHIFT, 1)
+        opts = sped.solve_opts(sped.MU_EG, 2.0 / info.lambda_star, torch.float64, torch.float64,
+                               max_steps=5000, check_every=10, tol=1e-5,
+                               refine_dtype=torch.float64)
+        vt = torch.float64
+    else:
+        G.set_polynomial(sped.POLY_LIMIT_EXP, 7)
+        if arm == "dilated_fp64":
+            opts = sped.solve_opts(sped.MU_EG, 1.5, torch.float64, torch.float64, max_steps=400,
+                                   tol=1e-5, refine_dtype=torch.float64)
+            vt = torch.float64
+        elif arm == "dilated_oja":
+            opts = sped.solve_opts(sped.OJA, 0.0, torch.float64, torch.float64, max_steps=200,
+                                   tol=1e-5, refine_dtype=torch.float64)
+            vt = torch.float64
+        else:
+            opts = sped.solve_opts(sped.MU_EG, 1.5, torch.bfloat16, torch.float32, max_steps=400,
+                                   tol=1e-5, switch_tol=3e-3, phase1_steps=100,
+                                   refine_dtype=torch.float32)
+            vt = torch.float32
+    V = to_block(V0, vt)
+    lam_gpu, rep = sped.solve_bottom_k(G, V, k, opts)
+    assert rep["converged"], rep
+    got = host(V, k)
+    ang = oracle.principal_angle_max(Ustar, got)
+    assert ang <= 1e-3, (arm, ang, rep)
+    # Rayleigh quotients of L on the converged subspace match the true bottom eigenvalues
+    Q = oracle.orthonormal_basis(got)
+    ritz = np.linalg.eigvalsh(Q.T @ oracle.laplacian_apply(g, Q))
+    assert np.allclose(ritz, lam, atol=1e-4, rtol=1e-5)
+    # the reported per-vector quotients equal the oracle's on the returned V
+    assert np.allclose(lam_gpu, oracle.ritz_values(got, oracle.laplacian_apply(g, got)),
+                       rtol=1e-9, atol=1e-12)
+
+
+def test_cluster_assign_config1_labels_bit_exact():
+    g = _config1()
+    k = 4
+    lam, U = oracle.bottom_k(g, k)
+    for dtype in (torch.float64, torch.float32):
+        V = to_block(U, dtype)
+        labels, iters = sped.cluster_assign(V, k, 4, seed=5)
+        want = oracle.kmeans(stored(U, dtype), 4, seed=5)
+        assert np.array_equal(labels.cpu().numpy(), want)
+    # well-separated nodes (majority of neighbours inside the block) carry the planted labels
+    deg = np.diff(g.row_ptr)
+    rows = np.repeat(np.arange(g.n), deg)
+    same = np.bincount(rows, weights=(g.labels[rows] == g.labels[g.col_idx]), minlength=g.n)
+    sep = same > deg / 2
+    lab = labels.cpu().numpy()
+    planted = g.labels
+    # labels are canonical by first occurrence, planted blocks are in node order too
+    assert np.array_equal(lab[sep], planted[sep])
+
+
+def test_cluster_assign_cliques_and_empty_restart():
+    g = gen.cliques([40, 25, 60, 10, 30])
+    lam, U = oracle.bottom_k(g, 5)
+    V = to_block(U, torch.float64)
+    labels, _ = sped.cluster_assign(V, 5, 5, seed=1)
+    assert np.array_equal(labels.cpu().numpy(), g.labels)
+    X = np.repeat(np.eye(3), [5, 1, 4], axis=0) * 10.0
+    V = to_block(X, torch.float64)
+    for seed in range(6):
+        labels, _ = sped.cluster_assign(V, 3, 4, seed=seed)
+        assert np.array_equal(labels.cpu().numpy(), oracle.kmeans(X, 4, seed=seed))
+
+
+def test_rayleigh_on_closed_form_eigenvectors():
+    n = 300
+    g = gen.path(n)
+    G = sped.Graph.from_csr(g)
+    i = np.arange(n)
+    js = [1, 2, 5, 17]
+    U = np.stack([np.cos(np.pi * j * (i + 0.5) / n) for j in js], axis=1)
+    V = to_block(U, torch.float64)
+    lam = sped.rayleigh(G, V, len(js)).cpu().numpy()
+    assert np.allclose(lam, [2 - 2 * np.cos(np.pi * j / n) for j in js], rtol=1e-12)
