@@ -23,7 +23,7 @@ import numpy as np
 
 __all__ = [
     "CSRGraph", "from_edges", "path", "cycle", "complete", "star", "grid", "cliques",
-    "sbm", "sbm_by_degree", "chung_lu_clusters", "batched_sbm", "concat_graphs",
+    "sbm", "sbm_regular", "sbm_by_degree", "chung_lu_clusters", "batched_sbm", "concat_graphs",
     "random_graph", "three_room_grid", "gaussian_block", "uniform_edge_weights",
     "undirected_edges", "DEFAULT_SEED",
 ]
@@ -212,6 +212,33 @@ def sbm(n: int, n_blocks: int, p_in: float, p_out: float, seed: int = DEFAULT_SE
     if permute:
         g = _permute(g, rng.permutation(n))
     return g
+
+
+def sbm_regular(n: int, n_blocks: int, d_in: int, d_out: int, seed: int = DEFAULT_SEED) -> CSRGraph:
+    """Near-regular stochastic block model by the configuration model: every node gets d_in
+    stubs paired uniformly inside its block and d_out stubs paired uniformly across blocks
+    (self loops, same-block cross pairs and duplicates dropped). Same block structure and mean
+    degree as ``sbm`` with p_in (b-1) = d_in, p_out (n-b) = d_out, without the Poisson
+    low-degree tail whose localized eigenvectors crowd the bottom of the spectrum."""
+    rng = np.random.default_rng(seed)
+    base = n // n_blocks
+    sizes = np.full(n_blocks, base, dtype=np.int64)
+    sizes[-1] += n - base * n_blocks
+    labels = np.repeat(np.arange(n_blocks), sizes)
+    stubs = np.repeat(np.arange(n, dtype=np.int64), d_in)
+    order = np.lexsort((rng.random(len(stubs)), labels[stubs]))
+    s = stubs[order]
+    bl = labels[s]
+    m = len(s) // 2
+    a, b = s[0:2 * m:2], s[1:2 * m:2]
+    keep = bl[0:2 * m:2] == bl[1:2 * m:2]
+    a, b = a[keep], b[keep]
+    out = rng.permutation(np.repeat(np.arange(n, dtype=np.int64), d_out))
+    m2 = len(out) // 2
+    c, d = out[0:2 * m2:2], out[1:2 * m2:2]
+    cross = labels[c] != labels[d]
+    return from_edges(n, np.concatenate([a, c[cross]]), np.concatenate([b, d[cross]]),
+                      labels=labels, name=f"sbmreg{n}x{n_blocks}")
 
 
 def sbm_by_degree(n: int, n_blocks: int, mean_degree: float, intra_frac: float,

@@ -79,7 +79,8 @@ sped_status sped_workspace_size(int64_t n, int64_t nnz, size_t *bytes);
 /* Validate the CSR (when check != 0), derive the reverse-entry map, the undirected edge list
  * (edges numbered by the CSR order of their upper entries a < b), weighted degrees and the
  * spectral bound lambda_max <= 2 max_i d_i (Section 5.4). row_ptr/col_idx (and d_w when not
- * NULL) must stay valid while the graph is used; d_workspace holds the derived arrays.
+ * NULL) must stay valid while the graph is used; col_idx and w must be 16-byte aligned (the
+ * chain kernel reads them in 16-byte quads); d_workspace holds the derived arrays.
  * Synchronises the stream. On success *out receives a graph handle; the default polynomial
  * is SPED_POLY_SHIFT with lambda* = the spectral bound. */
 sped_status sped_build_laplacian(int64_t n, int64_t nnz, const int32_t *d_row_ptr,

@@ -374,6 +374,9 @@ sped_status sped_build_laplacian(int64_t n, int64_t nnz, const int32_t *d_row_pt
     if (!d_row_ptr || (nnz > 0 && !d_col_idx))
         return fail(SPED_ERR_INVALID_ARG, "build_laplacian: null CSR array");
     if (nnz % 2) return fail(SPED_ERR_BAD_CSR, "odd nnz cannot be a symmetric adjacency");
+    if (((uintptr_t)d_col_idx) % 16 || ((uintptr_t)d_w) % 16 || ((uintptr_t)d_row_ptr) % 4)
+        return fail(SPED_ERR_INVALID_ARG,
+                    "build_laplacian: col_idx and w must be 16-byte aligned (row_ptr 4-byte)");
     WsLayout L = ws_layout(n, nnz);
     if (!d_workspace || ws_bytes < L.total || ((uintptr_t)d_workspace) % 256)
         return fail(SPED_ERR_SCRATCH, "build_laplacian: workspace needs %zu bytes, 256-aligned",

@@ -57,21 +57,26 @@ __device__ __forceinline__ void finish_row(const StepArgs<Tx, Tv, Ty, A, W, HV> 
 }
 
 // accumulate neighbours [p, p1) of the lane's chunk into acc / dsum
-template <typename Tx, typename Tv, typename Ty, typename A, bool W, bool HV, int E>
-__device__ __forceinline__ void gather_range(const StepArgs<Tx, Tv, Ty, A, W, HV> &a, int c, int p,
-                                             int p1, A (&acc)[E], A &dsum) {
+// accumulate neighbours [p, p1) of the lane's chunk into acc / dsum; column indices and weights
+// come from `cs` / `ws` at offset `off` (a shared-memory tile, or the global arrays with off 0)
+template <typename Tx, typename Tv, typename Ty, typename A, bool W, bool HV, int E, bool SHARED>
+__device__ __forceinline__ void gather_from(const StepArgs<Tx, Tv, Ty, A, W, HV> &a, int c, int p,
+                                            int p1, const int32_t *cs, const float *ws, int off,
+                                            A (&acc)[E], A &dsum) {
     const Tx *Xc = a.X + c * E;
+    auto col = [&](int q) { return SHARED ? cs[q - off] : __ldg(cs + q); };
+    auto wgt = [&](int q) { return SHARED ? ws[q - off] : __ldg(ws + q); };
     for (; p + UNROLL <= p1; p += UNROLL) {
         int j[UNROLL];
 #pragma unroll
-        for (int u = 0; u < UNROLL; ++u) j[u] = __ldg(a.ci + p + u);
+        for (int u = 0; u < UNROLL; ++u) j[u] = col(p + u);
         A x[UNROLL][E];
 #pragma unroll
         for (int u = 0; u < UNROLL; ++u) load_chunk<Tx, E, A>(Xc + (int64_t)j[u] * a.ldx, x[u]);
         if constexpr (W) {
             A wv[UNROLL];
 #pragma unroll
-            for (int u = 0; u < UNROLL; ++u) wv[u] = (A)__ldg(a.w + p + u);
+            for (int u = 0; u < UNROLL; ++u) wv[u] = (A)wgt(p + u);
 #pragma unroll
             for (int u = 0; u < UNROLL; ++u) {
                 dsum += wv[u];
@@ -86,11 +91,11 @@ __device__ __forceinline__ void gather_range(const StepArgs<Tx, Tv, Ty, A, W, HV
         }
     }
     for (; p < p1; ++p) {
-        int j = __ldg(a.ci + p);
+        int j = col(p);
         A x[E];
         load_chunk<Tx, E, A>(Xc + (int64_t)j * a.ldx, x);
         if constexpr (W) {
-            A wv = (A)__ldg(a.w + p);
+            A wv = (A)wgt(p);
             dsum += wv;
 #pragma unroll
             for (int i = 0; i < E; ++i) acc[i] += wv * x[i];
@@ -101,9 +106,48 @@ __device__ __forceinline__ void gather_range(const StepArgs<Tx, Tv, Ty, A, W, HV
     }
 }
 
+template <typename Tx, typename Tv, typename Ty, typename A, bool W, bool HV, int E>
+__device__ __forceinline__ void gather_range(const StepArgs<Tx, Tv, Ty, A, W, HV> &a, int c, int p,
+                                             int p1, A (&acc)[E], A &dsum) {
+    gather_from<Tx, Tv, Ty, A, W, HV, E, false>(a, c, p, p1, a.ci, a.w, 0, acc, dsum);
+}
+
+// L2 policy for data read once per step (column indices, weights): evict first, so the
+// gathered block and the block being written keep their L2 lines.
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+__device__ __forceinline__ int4 ld_stream_v4(const int4 *p, uint64_t pol) {
+    int4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.s32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p), "l"(pol));
+    return v;
+}
+
+// Four column indices (and weights) of the aligned quad starting at q (q % 4 == 0): one 16-byte
+// streaming load when the quad lies inside the array, element loads at the array's end.
+__device__ __forceinline__ int4 quad_i32(const int32_t *__restrict__ src, int q, int total,
+                                         uint64_t pol) {
+    if (q + 4 <= total) return ld_stream_v4(reinterpret_cast<const int4 *>(src + q), pol);
+    int4 v = make_int4(0, 0, 0, 0);
+    if (q + 0 < total) v.x = __ldg(src + q + 0);
+    if (q + 1 < total) v.y = __ldg(src + q + 1);
+    if (q + 2 < total) v.z = __ldg(src + q + 2);
+    return v;
+}
+
+// Row-group schedule. Each lane walks its row's neighbours in aligned quads of the CSR column
+// array: one 16-byte request brings four indices (weights alike), the next quad is requested
+// while the current quad's four gathers are in flight, and index/weight loads carry an L2
+// evict-first policy so the gathered block keeps its L2 lines. Entries of an edge quad that
+// belong to the neighbouring rows are skipped.
 template <typename Tx, typename Tv, typename Ty, typename A, bool W, bool HV>
 __global__ void __launch_bounds__(STEP_THREADS)
-k_step_rowgroup(StepArgs<Tx, Tv, Ty, A, W, HV> a, int rows_per_warp) {
+k_step_rowgroup(StepArgs<Tx, Tv, Ty, A, W, HV> a, int rows_per_warp, int nnz) {
     constexpr int E = 16 / (int)sizeof(Tx);
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * STEP_THREADS + threadIdx.x) >> 5;
@@ -117,7 +161,53 @@ k_step_rowgroup(StepArgs<Tx, Tv, Ty, A, W, HV> a, int rows_per_warp) {
 #pragma unroll
     for (int i = 0; i < E; ++i) acc[i] = A(0);
     A dsum = A(0);
-    gather_range<Tx, Tv, Ty, A, W, HV, E>(a, c, p0, p1, acc, dsum);
+    const Tx *Xc = a.X + c * E;
+    const uint64_t pol = l2_evict_first_policy();
+    int q = p0 & ~3;
+    int4 jj = make_int4(0, 0, 0, 0), jn = jj;
+    float4 ww = make_float4(0.f, 0.f, 0.f, 0.f), wn = ww;
+    if (q < p1) {
+        jn = quad_i32(a.ci, q, nnz, pol);
+        if constexpr (W) {
+            int4 t = quad_i32(reinterpret_cast<const int32_t *>(a.w), q, nnz, pol);
+            wn = make_float4(__int_as_float(t.x), __int_as_float(t.y), __int_as_float(t.z),
+                             __int_as_float(t.w));
+        }
+    }
+    for (; q < p1; q += 4) {
+        jj = jn;
+        ww = wn;
+        const int j[4] = {jj.x, jj.y, jj.z, jj.w};
+        bool ok[4];
+        A x[4][E];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            ok[u] = (q + u >= p0) && (q + u < p1);
+            if (ok[u]) load_chunk<Tx, E, A>(Xc + (int64_t)j[u] * a.ldx, x[u]);
+        }
+        if (q + 4 < p1) {  // next quad while the gathers are in flight
+            jn = quad_i32(a.ci, q + 4, nnz, pol);
+            if constexpr (W) {
+                int4 t = quad_i32(reinterpret_cast<const int32_t *>(a.w), q + 4, nnz, pol);
+                wn = make_float4(__int_as_float(t.x), __int_as_float(t.y), __int_as_float(t.z),
+                                 __int_as_float(t.w));
+            }
+        }
+        const float wq[4] = {ww.x, ww.y, ww.z, ww.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (!ok[u]) continue;
+            if constexpr (W) {
+                const A wu = (A)wq[u];
+                dsum += wu;
+#pragma unroll
+                for (int i = 0; i < E; ++i) acc[i] += wu * x[u][i];
+            } else {
+#pragma unroll
+                for (int i = 0; i < E; ++i) acc[i] += x[u][i];
+            }
+        }
+    }
     if constexpr (!W) dsum = (A)(p1 - p0);
     finish_row<Tx, Tv, Ty, A, W, HV, E>(a, r, c, acc, dsum);
 }
@@ -353,7 +443,10 @@ static sped_status run_step(const sped_graph *g, int k, const void *X, int ldx, 
     if (!use_merge(g, split)) {
         int64_t warps = (g->n + per_warp - 1) / per_warp;
         int64_t blocks = (warps * 32 + STEP_THREADS - 1) / STEP_THREADS;
-        if (blocks > 0) k_step_rowgroup<Tx, Tv, Ty, A, W, HV><<<(unsigned)blocks, STEP_THREADS, 0, st>>>(a, per_warp);
+        // quad loads of col_idx / w need 16-byte aligned arrays (checked at graph set-up)
+        if (blocks > 0)
+            k_step_rowgroup<Tx, Tv, Ty, A, W, HV><<<(unsigned)blocks, STEP_THREADS, 0, st>>>(
+                a, per_warp, (int)g->nnz);
         SPED_CHECK_LAUNCH("k_step_rowgroup");
         return SPED_OK;
     }

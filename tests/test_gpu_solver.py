@@ -27,6 +27,8 @@ def test_gram(at, bt, tol, n, ka, kb):
     torch.cuda.synchronize()
     M = stored(A0, at) if not kb else np.concatenate([stored(A0, at), stored(B0, bt)], axis=1)
     want = M.T @ M
+    if not kb and at != torch.float64:
+        tol = max(tol, 2e-6)  # A alone: products in F32
     got = G.cpu().numpy()
     assert np.array_equal(got, got.T)
     assert rel(got, want) <= tol
