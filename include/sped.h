@@ -173,6 +173,23 @@ sped_status sped_gram(int64_t n, const void *d_A, sped_dtype a_t, int lda, int k
 
 sped_status sped_gram_scratch_size(int64_t n, int ka, int kb, size_t *bytes);
 
+/* sped_gram for callers that cannot allocate device memory: for example code running inside a
+ * host callback, a real-time loop or a plugin host, where cudaMalloc (which may synchronise the
+ * device) is not allowed and no device allocator is handed in. The paper has no counterpart;
+ * this is a deployment variant of sped_gram with the same arguments minus the scratch buffer
+ * and the same result (within the same rounding).
+ *  - Scratch: a fixed 4 MiB static device array inside the library (held by every GPU that
+ *    loads the library until the process exits). Maximum size: ka + kb <= 64, any n; larger
+ *    column counts are rejected with SPED_ERR_UNSUPPORTED before anything is launched.
+ *  - Set-up: the first call on each device looks up the array's device address (with that
+ *    device current); make that first call before any stream capture.
+ *  - Concurrency: all calls share the array and overwrite it; calls that overlap on the GPU
+ *    (different streams or host threads) race and must be serialised by the caller.
+ *  - Allocates nothing: no cudaMalloc, cudaFree or allocating library routine. */
+sped_status sped_gram_noalloc(int64_t n, const void *d_A, sped_dtype a_t, int lda, int ka,
+                              const void *d_B, sped_dtype b_t, int ldb, int kb, double *d_G,
+                              void *stream);
+
 /* ------------------------------------------------------------------------------------
  * One solver step on the graph's operator M (Section 5.1: mu-EG and Oja; Section 3 for the
  * reversal). V (n x k, F32 or F64 master copy, k <= 32) is updated in place:
@@ -262,6 +279,7 @@ sped_status sped_cluster_assign(const void *d_V, sped_dtype v_t, int64_t n, int 
                                 int *h_iters, void *d_scratch, size_t scratch_bytes, void *stream);
 
 sped_status sped_cluster_scratch_size(int64_t n, int k, int n_clusters, size_t *bytes);
+
 
 /* ------------------------------------------------------------------------------------ */
 const char *sped_last_error(void);

@@ -5,6 +5,8 @@
 // 4x4 register blocks of the upper triangle per thread, F32 accumulation over a short window
 // of rows (exact products for BF16 inputs) and F64 accumulation across windows; per-CTA F64
 // partials reduced in a fixed order (deterministic).
+#include <mutex>
+
 #include "sped_internal.cuh"
 
 namespace sped {
@@ -247,3 +249,91 @@ sped_status sped_gram(int64_t n, const void *d_A, sped_dtype a_t, int lda, int k
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------
+// Gram with no caller scratch, for callers that may not allocate device memory at all.
+//
+// The per-CTA partial sums live in a fixed 4 MiB array of static device memory instead of a
+// caller-provided buffer. Every GPU that loads this library holds that array until the
+// process exits. The array's name is only a host-side stand-in, so its device address is
+// looked up with cudaGetSymbolAddress once per device (with that device current) on the first
+// call made on that device; make that first call before any stream capture. The kernels are
+// the ones sped_gram launches; only fewer CTAs are used when the partials would not fit.
+// Each call writes every partial it later reads, so nothing has to start at zero. All calls
+// share the one array: calls that overlap on the GPU (other streams, other host threads)
+// race on it and must be serialised by the caller.
+// ---------------------------------------------------------------------------------------
+namespace sped {
+
+constexpr size_t GRAM_STATIC_DOUBLES = 512 * 1024;  // 4 MiB
+constexpr int GRAM_STATIC_MAX_DEVICES = 64;
+
+static __device__ __align__(256) double g_gram_static_partials[GRAM_STATIC_DOUBLES];
+
+static double *g_gram_static_addr[GRAM_STATIC_MAX_DEVICES];
+static std::mutex g_gram_static_mu;
+
+static sped_status gram_static_address(double **out) {
+    int dev = 0;
+    SPED_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= GRAM_STATIC_MAX_DEVICES)
+        return fail(SPED_ERR_UNSUPPORTED, "gram_noalloc: device ordinal %d >= %d", dev,
+                    GRAM_STATIC_MAX_DEVICES);
+    std::lock_guard<std::mutex> lock(g_gram_static_mu);
+    if (!g_gram_static_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_gram_static_partials);
+        if (e != cudaSuccess || !p) return cuda_fail(e, "gram_noalloc: cudaGetSymbolAddress");
+        g_gram_static_addr[dev] = (double *)p;
+    }
+    *out = g_gram_static_addr[dev];
+    return SPED_OK;
+}
+
+}  // namespace sped
+
+extern "C" sped_status sped_gram_noalloc(int64_t n, const void *d_A, sped_dtype a_t, int lda,
+                                         int ka, const void *d_B, sped_dtype b_t, int ldb, int kb,
+                                         double *d_G, void *stream) {
+    if (n < 0 || !d_G) return fail(SPED_ERR_INVALID_ARG, "gram_noalloc: bad n or null G");
+    if (!dtype_valid(a_t) || (kb > 0 && !dtype_valid(b_t)))
+        return fail(SPED_ERR_INVALID_ARG, "gram_noalloc: dtype");
+    if (ka < 1 || lda < ka || !d_A) return fail(SPED_ERR_INVALID_ARG, "gram_noalloc: A layout");
+    if (kb < 0 || (kb > 0 && (ldb < kb || !d_B)))
+        return fail(SPED_ERR_INVALID_ARG, "gram_noalloc: B layout");
+    if (ka + kb > GRAM_MAXK)
+        return fail(SPED_ERR_UNSUPPORTED,
+                    "gram_noalloc: ka + kb = %d exceeds the maximum of %d columns", ka + kb,
+                    GRAM_MAXK);
+    const GramShape sh = gram_shape(ka, kb);
+    const size_t per_cta = (size_t)sh.P * 16;
+    if (per_cta > GRAM_STATIC_DOUBLES)
+        return fail(SPED_ERR_UNSUPPORTED, "gram_noalloc: partials exceed the static array");
+    double *partial = nullptr;
+    SPED_TRY(gram_static_address(&partial));
+    cudaStream_t st = as_stream(stream);
+    if (n == 0) {
+        SPED_CUDA(cudaMemsetAsync(d_G, 0, sizeof(double) * sh.K2 * sh.K2, st));
+        return SPED_OK;
+    }
+    int ctas = gram_ctas(n);
+    const int fit = (int)(GRAM_STATIC_DOUBLES / per_cta);
+    if (ctas > fit) ctas = fit;
+    if (kb == 0) {
+        d_B = d_A;
+        b_t = a_t;
+        ldb = lda;
+    }
+#define G2(TA, TB) return run_gram<TA, TB>(n, d_A, lda, ka, d_B, ldb, kb, d_G, partial, ctas, st)
+    if (a_t == SPED_F32 && b_t == SPED_F32) G2(float, float);
+    if (a_t == SPED_BF16 && b_t == SPED_BF16) G2(bf16, bf16);
+    if (a_t == SPED_F32 && b_t == SPED_BF16) G2(float, bf16);
+    if (a_t == SPED_BF16 && b_t == SPED_F32) G2(bf16, float);
+    if (a_t == SPED_F64 && b_t == SPED_F64) G2(double, double);
+    if (a_t == SPED_F32 && b_t == SPED_F64) G2(float, double);
+    if (a_t == SPED_F64 && b_t == SPED_F32) G2(double, float);
+    if (a_t == SPED_BF16 && b_t == SPED_F64) G2(bf16, double);
+    if (a_t == SPED_F64 && b_t == SPED_BF16) G2(double, bf16);
+#undef G2
+    return fail(SPED_ERR_UNSUPPORTED, "gram_noalloc: dtypes %d/%d", (int)a_t, (int)b_t);
+}
