@@ -280,6 +280,75 @@ sped_status sped_cluster_assign(const void *d_V, sped_dtype v_t, int64_t n, int 
 
 sped_status sped_cluster_scratch_size(int64_t n, int k, int n_clusters, size_t *bytes);
 
+/* ------------------------------------------------------------------------------------
+ * Batched: many independent graphs solved in one persistent launch (the stochastic-block
+ * workloads of Section 5.4 at scale). The graphs are given as one block-diagonal CSR: graph g
+ * owns rows [node_off[g], node_off[g+1]) and its columns stay in that range (global ids).
+ * Each CTA takes whole graphs from a work list ordered by decreasing size and runs complete
+ * mu-EG steps on them with the limit form (I - s_g L_g)^l, s_g from the automatic rule of
+ * sped_set_polynomial applied to each graph's own spectral bound. No CTA waits on another;
+ * one call is a memset plus one kernel launch, so it can be captured in a CUDA graph.
+ * ------------------------------------------------------------------------------------ */
+typedef struct sped_batch sped_batch;
+
+sped_status sped_batch_workspace_size(int64_t n_graphs, size_t *bytes);
+
+/* h_node_off: host, n_graphs+1 offsets (node_off[0] = 0, every graph non-empty). degree: odd l.
+ * check != 0 verifies that columns stay inside their graph, rows sorted, no self loops.
+ * Synchronises the stream. */
+sped_status sped_batch_create(int64_t n_graphs, const int64_t *h_node_off,
+                              const int32_t *d_row_ptr, const int32_t *d_col_idx,
+                              const float *d_w, int degree, int check, void *d_workspace,
+                              size_t ws_bytes, void *stream, sped_batch **out);
+
+void sped_batch_destroy(sped_batch *b);
+
+/* Per-graph limit-form scale s_g (host, n_graphs doubles). */
+sped_status sped_batch_scale(const sped_batch *b, double *h_scale, int capacity);
+
+sped_status sped_batch_scratch_size(const sped_batch *b, int k, sped_dtype chain_t,
+                                    size_t *bytes);
+
+/* `steps` mu-EG steps (Section 5.1) on every graph. V: F32, n_total x ld, ld >= 8 (k <= 8) or
+ * ld >= 16 (k <= 16), 16-byte aligned, updated in place. chain_t: BF16 or F32 storage of the
+ * intermediate products (F32 accumulation). d_ritz: n_graphs x k doubles, the Rayleigh
+ * quotients of each graph's operator before its last update. */
+sped_status sped_batch_eig_steps(const sped_batch *b, int steps, double eta, sped_dtype chain_t,
+                                 float *d_V, int k, int ld, double *d_ritz, void *d_scratch,
+                                 size_t scratch_bytes, void *stream);
+
+/* ------------------------------------------------------------------------------------
+ * Differentiable utilities (the solver family of Section 5.1 as a loss): with H = V^T M V
+ * (k x k, e.g. the block H = G[0:k, k:2k] of sped_gram(V, M V), ldh = 2k),
+ *   u_i = H_ii - sum_{j<i} H_ij^2 / H_jj.
+ * d_g (k doubles, may be NULL): weights of the loss sum_i g_i u_i; d_Hbar (k x k, row-major,
+ * needs d_g) receives d(sum g_i u_i)/dH with every entry H_ij treated as independent; d_S
+ * (k x k, may be NULL) receives the detached-parents coefficients: du_i/dv_i (v_j, j < i,
+ * held fixed) = sum_j y_j S[j][i]. Any output may be NULL. k <= 32, one CTA, FP64.
+ * ------------------------------------------------------------------------------------ */
+sped_status sped_eg_utilities(int k, const double *d_H, int ldh, const double *d_g, double *d_u,
+                              double *d_Hbar, double *d_S, void *stream);
+
+/* Out = A P + B Q for n x k blocks (F32 or F64, type t) and k x k row-major FP64 matrices
+ * (Out[r][i] = sum_j A[r][j] P[j][i] + B[r][j] Q[j][i]); d_B may be NULL. Out must not
+ * overlap A or B. k <= 32. */
+sped_status sped_block_combine(int64_t n, int k, const void *d_A, int lda, const double *d_P,
+                               const void *d_B, int ldb, const double *d_Q, void *d_Out, int ldo,
+                               sped_dtype t, void *stream);
+
+/* Edge-weight gradient of f(H), H = V^T M V, for the limit form M = B^l, B = I - sL (V fixed):
+ *   df/dw_e = -s sum_{t=0}^{l-1} (x_e^T B^t V) Hbar (x_e^T B^{l-1-t} V)^T,
+ * x_e the incidence row of undirected edge e (dL/dw_e = x_e x_e^T). d_HbarT: k x k row-major
+ * FP64 holding Hbar transposed (d_HbarT[j*k+i] = Hbar[i][j]). d_grad: n_edges doubles, edge
+ * order of sped_graph_edges. The chains B^t V and B^u V Hbar^T are kept at every
+ * ceil(sqrt(l))-th step and recomputed between, so scratch holds about 2 sqrt(l) blocks.
+ * V: F32 or F64 (the chains and the SDDMM run in that type, accumulated in FP64). */
+sped_status sped_edge_grad(const sped_graph *g, const void *d_V, sped_dtype v_t, int k, int ld,
+                           const double *d_HbarT, double *d_grad, void *d_scratch,
+                           size_t scratch_bytes, void *stream);
+
+sped_status sped_edge_grad_scratch_size(const sped_graph *g, int k, sped_dtype v_t,
+                                        size_t *bytes);
 
 /* ------------------------------------------------------------------------------------ */
 const char *sped_last_error(void);

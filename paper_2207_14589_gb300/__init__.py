@@ -382,3 +382,210 @@ def cluster_assign(V, k, n_clusters, seed=0, max_iter=100, stream=None):
                                      _ptr(labels), ctypes.byref(iters), _ptr(scr), nb.value,
                                      _stream(stream)))
     return labels, iters.value
+
+
+# ----------------------------------------------------------------------------------------
+# batched: many graphs in one persistent launch
+# ----------------------------------------------------------------------------------------
+class Batch:
+    """Independent graphs stored as one block-diagonal CSR (global node ids), solved together
+    by sped_batch_eig_steps."""
+
+    def __init__(self, node_off, row_ptr, col_idx, w=None, degree=31, check=True, stream=None):
+        L = lib()
+        _batch_sigs(L)
+        self.node_off = [int(x) for x in node_off]
+        self.n_graphs = len(self.node_off) - 1
+        self.row_ptr = row_ptr.to(torch.int32).contiguous()
+        self.col_idx = col_idx.to(torch.int32).contiguous()
+        self.w = None if w is None else w.to(torch.float32).contiguous()
+        self.n_total = self.node_off[-1]
+        self.device = self.row_ptr.device
+        nb = ctypes.c_size_t()
+        _check(L.sped_batch_workspace_size(self.n_graphs, ctypes.byref(nb)))
+        self.workspace = _scratch(nb.value, self.device)
+        off = (ctypes.c_int64 * (self.n_graphs + 1))(*self.node_off)
+        h = ctypes.c_void_p()
+        _check(L.sped_batch_create(self.n_graphs, off, _ptr(self.row_ptr), _ptr(self.col_idx),
+                                   _ptr(self.w), int(degree), int(check), _ptr(self.workspace),
+                                   nb.value, _stream(stream), ctypes.byref(h)))
+        self.handle = h
+        self.degree = degree
+
+    @classmethod
+    def from_graphs(cls, graphs, degree=31, device="cuda", check=True):
+        import gen as _gen  # input generators only (no method arithmetic)
+        big, node_off, _ = _gen.concat_graphs(graphs)
+        rp = torch.from_numpy(big.row_ptr).to(device)
+        ci = torch.from_numpy(big.col_idx).to(device)
+        w = None if big.w is None else torch.from_numpy(big.w).to(device)
+        return cls(node_off, rp, ci, w, degree=degree, check=check)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h and _lib is not None:
+            _lib.sped_batch_destroy(h)
+            self.handle = None
+
+    def scales(self):
+        out = (ctypes.c_double * self.n_graphs)()
+        _check(lib().sped_batch_scale(self.handle, out, self.n_graphs))
+        return list(out)
+
+    def scratch_bytes(self, k, chain_dtype=torch.bfloat16):
+        nb = ctypes.c_size_t()
+        _check(lib().sped_batch_scratch_size(self.handle, k, _TORCH_DT[chain_dtype],
+                                             ctypes.byref(nb)))
+        return nb.value
+
+    def eig_steps(self, V, k, steps=1, eta=1.0, chain_dtype=torch.bfloat16, ritz=None,
+                  scratch=None, stream=None):
+        if V.dtype != torch.float32 or V.dim() != 2 or V.stride(1) != 1:
+            raise ValueError("batched V must be a 2-D float32 block")
+        if ritz is None:
+            ritz = torch.empty((self.n_graphs, k), dtype=torch.float64, device=V.device)
+        if scratch is None:
+            scratch = _scratch(self.scratch_bytes(k, chain_dtype), V.device)
+        _check(lib().sped_batch_eig_steps(self.handle, int(steps), float(eta),
+                                          _TORCH_DT[chain_dtype], _ptr(V), k, V.stride(0),
+                                          _ptr(ritz), _ptr(scratch), scratch.numel(),
+                                          _stream(stream)))
+        return V, ritz
+
+
+def batch_block(n_total, k, device="cuda"):
+    """Float32 master block for the batched solver (ld 8 for k <= 8, else 16)."""
+    return torch.zeros((n_total, 8 if k <= 8 else 16), dtype=torch.float32, device=device)
+
+
+_batch_ready = False
+
+
+def _batch_sigs(L):
+    global _batch_ready
+    if _batch_ready:
+        return
+    vp, i32, i64, dbl, sz = (ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double,
+                             ctypes.c_size_t)
+    P = ctypes.POINTER
+    for name, args in {
+        "sped_batch_workspace_size": [i64, P(sz)],
+        "sped_batch_create": [i64, P(ctypes.c_int64), vp, vp, vp, i32, i32, vp, sz, vp, P(vp)],
+        "sped_batch_scale": [vp, P(dbl), i32],
+        "sped_batch_scratch_size": [vp, i32, i32, P(sz)],
+        "sped_batch_eig_steps": [vp, i32, dbl, i32, vp, i32, i32, vp, vp, sz, vp],
+    }.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    L.sped_batch_destroy.argtypes = [vp]
+    L.sped_batch_destroy.restype = None
+    _batch_ready = True
+
+
+# ----------------------------------------------------------------------------------------
+# differentiable utilities
+# ----------------------------------------------------------------------------------------
+_diff_ready = False
+
+
+def _diff_sigs(L):
+    global _diff_ready
+    if _diff_ready:
+        return
+    vp, i32, i64, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_size_t
+    P = ctypes.POINTER
+    for name, args in {
+        "sped_eg_utilities": [i32, vp, i32, vp, vp, vp, vp, vp],
+        "sped_block_combine": [i64, i32, vp, i32, vp, vp, i32, vp, vp, i32, i32, vp],
+        "sped_edge_grad": [vp, vp, i32, i32, i32, vp, vp, vp, sz, vp],
+        "sped_edge_grad_scratch_size": [vp, i32, i32, P(sz)],
+    }.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    _diff_ready = True
+
+
+def eg_utilities(G, k, g_u=None, stream=None):
+    """From the Gram G = [V Y]^T [V Y] (2k x 2k FP64, Y = M V): utilities u (k), and when
+    g_u is given Hbar = d(sum g_i u_i)/dH; also the detached-parents coefficients S."""
+    L = lib()
+    _diff_sigs(L)
+    dev = G.device
+    H = G[:, k:]  # rows 0..k-1 used, row stride 2k
+    u = torch.empty(k, dtype=torch.float64, device=dev)
+    S = torch.empty((k, k), dtype=torch.float64, device=dev)
+    Hbar = None
+    gg = None
+    if g_u is not None:
+        gg = g_u.to(dtype=torch.float64, device=dev).contiguous()
+        Hbar = torch.empty((k, k), dtype=torch.float64, device=dev)
+    _check(L.sped_eg_utilities(k, ctypes.c_void_p(H.data_ptr()), G.stride(0), _ptr(gg), _ptr(u),
+                               _ptr(Hbar), _ptr(S), _stream(stream)))
+    return u, Hbar, S
+
+
+def block_combine(A, k, P, B=None, Q=None, out=None, stream=None):
+    """out = A P + B Q (n x k blocks, k x k FP64 coefficient matrices)."""
+    L = lib()
+    _diff_sigs(L)
+    t, lda = _block(A, k)
+    ldb = B.stride(0) if B is not None else 0
+    if out is None:
+        out = torch.zeros_like(A)
+    _check(L.sped_block_combine(A.shape[0], k, _ptr(A), lda, _ptr(P.contiguous()), _ptr(B), ldb,
+                                _ptr(Q.contiguous() if Q is not None else None), _ptr(out),
+                                out.stride(0), t, _stream(stream)))
+    return out
+
+
+def edge_grad(g: Graph, V, k, HbarT, stream=None):
+    """d f / d w_e for every undirected edge (FP64), f(H) with df/dH = Hbar."""
+    L = lib()
+    _diff_sigs(L)
+    t, ld = _block(V, k)
+    nb = ctypes.c_size_t()
+    _check(L.sped_edge_grad_scratch_size(g.handle, k, t, ctypes.byref(nb)))
+    scr = _scratch(nb.value, V.device)
+    out = torch.empty(g.info().n_edges, dtype=torch.float64, device=V.device)
+    _check(L.sped_edge_grad(g.handle, _ptr(V), t, k, ld, _ptr(HbarT.contiguous()), _ptr(out),
+                            _ptr(scr), nb.value, _stream(stream)))
+    return out
+
+
+class EigenGameUtility(torch.autograd.Function):
+    """u = EigenGame utilities of the columns of V under M = (I - sL(w))^l.
+
+    Inputs: V (n x ld padded block, F32 or F64; the first k columns are the players), w (one
+    weight per undirected edge, the graph's learnable weights), the Graph (limit form set) and
+    k. Backward: dV = Y Hbar^T + M (V Hbar) (adjoint polynomial chain) and dw by the
+    checkpointed SDDMM (sped_edge_grad). Every step runs in libsped's kernels."""
+
+    @staticmethod
+    def forward(ctx, V, w, graph, k):
+        graph.set_edge_weights(w.detach().to(torch.float32))
+        Y = torch.zeros_like(V)
+        apply_poly(graph, V, Y, k, chain_dtype=V.dtype)
+        G = gram(V, k, Y, k)
+        u, _, _ = eg_utilities(G, k)
+        ctx.save_for_backward(V, Y, G)
+        ctx.graph, ctx.k, ctx.w_dtype = graph, k, w.dtype
+        return u
+
+    @staticmethod
+    def backward(ctx, g_u):
+        V, Y, G = ctx.saved_tensors
+        graph, k = ctx.graph, ctx.k
+        _, Hbar, _ = eg_utilities(G, k, g_u)
+        T = block_combine(V, k, Hbar)                      # V Hbar
+        MT = torch.zeros_like(V)
+        apply_poly(graph, T, MT, k, chain_dtype=V.dtype)   # adjoint chain: M^T = M
+        eye = torch.eye(k, dtype=torch.float64, device=V.device)
+        dV = block_combine(Y, k, Hbar.t().contiguous(), MT, eye)
+        dw = edge_grad(graph, V, k, Hbar.t().contiguous())
+        return dV, dw.to(ctx.w_dtype), None, None
+
+
+def eigengame_utilities(V, w, graph, k):
+    return EigenGameUtility.apply(V, w, graph, k)
