@@ -156,7 +156,9 @@ size_t gram_scratch(int64_t n, int ka, int kb) {
     int64_t tiles = (n + GRAM_TILE - 1) / GRAM_TILE;
     int64_t c = 2LL * 256;  // upper bound on CTAs for any device this library supports
     if (tiles < c) c = tiles < 1 ? 1 : tiles;
-    p.add(sizeof(double) * (size_t)c * sh.P * 16);
+    const size_t core = sizeof(double) * (size_t)c * sh.P * 16;
+    const size_t tc = (ka + kb) <= 64 ? gram_tc_scratch(n, ka, kb) : 0;  // tensor path (BF16 too)
+    p.add(core > tc ? core : tc);
     return p.total();
 }
 
@@ -197,6 +199,8 @@ sped_status launch_gram(int64_t n, const void *A, sped_dtype at, int lda, int ka
     if (ka + kb > GRAM_MAXK || ka < 1 || kb < 0)
         return fail(SPED_ERR_UNSUPPORTED, "gram: ka + kb = %d (1..%d supported)", ka + kb,
                     GRAM_MAXK);
+    if (n > 0 && gram_tc_pieces(at, bt, ka, kb))  // F32 / BF16 inputs: tensor cores
+        return launch_gram_tc(n, A, at, lda, ka, B, bt, ldb, kb, G, scr, st);
     GramShape sh = gram_shape(ka, kb);
     int ctas = gram_ctas(n);
     double *partial = (double *)scr.take(sizeof(double) * (size_t)ctas * sh.P * 16);

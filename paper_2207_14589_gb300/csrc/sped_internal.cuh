@@ -281,6 +281,11 @@ size_t poly_step_scratch(const sped_graph *g, int k, sped_dtype xt, int split);
 sped_status launch_gram(int64_t n, const void *A, sped_dtype at, int lda, int ka, const void *B,
                         sped_dtype bt, int ldb, int kb, double *G, Scratch &scr, cudaStream_t st);
 size_t gram_scratch(int64_t n, int ka, int kb);
+int gram_tc_pieces(sped_dtype at, sped_dtype bt, int ka, int kb);
+size_t gram_tc_scratch(int64_t n, int ka, int kb);
+sped_status launch_gram_tc(int64_t n, const void *A, sped_dtype at, int lda, int ka, const void *B,
+                           sped_dtype bt, int ldb, int kb, double *G, Scratch &scr,
+                           cudaStream_t st);
 sped_status apply_poly_impl(const sped_graph *g, int k, const void *V, sped_dtype vt, int ldv,
                             void *Y, sped_dtype yt, int ldy, sped_dtype ct, sped_mode mode,
                             int64_t walkers, uint64_t seed, Scratch &scr, cudaStream_t st);
