@@ -199,7 +199,7 @@ sped_status launch_gram(int64_t n, const void *A, sped_dtype at, int lda, int ka
     if (ka + kb > GRAM_MAXK || ka < 1 || kb < 0)
         return fail(SPED_ERR_UNSUPPORTED, "gram: ka + kb = %d (1..%d supported)", ka + kb,
                     GRAM_MAXK);
-    if (n > 0 && gram_tc_pieces(at, bt, ka, kb))  // F32 / BF16 inputs: tensor cores
+    if (n > 0 && gram_tc_pieces(at, bt, ka, kb, lda, kb ? ldb : 0))  // F32/BF16: tensor cores
         return launch_gram_tc(n, A, at, lda, ka, B, bt, ldb, kb, G, scr, st);
     GramShape sh = gram_shape(ka, kb);
     int ctas = gram_ctas(n);

@@ -26,7 +26,8 @@
 
 namespace sped {
 
-constexpr int TC_THREADS = 128;
+constexpr int TC_THREADS = 256;
+constexpr int TC_MAXQ = 8;           // 16-byte chunks per thread per tile
 constexpr int TC_TILE = 128;          // graph rows per tile
 constexpr int TC_SLICES = TC_TILE / 16;
 constexpr int TC_SLICE_BYTES = 128 * 16 * 2;
@@ -122,6 +123,7 @@ k_gram_tc(int64_t n, const Ta *__restrict__ A, int lda, int ka, const Tb *__rest
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     TcSmem &sm = *reinterpret_cast<TcSmem *>(
         smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023));
+    constexpr int EA = 16 / (int)sizeof(Ta), EB = 16 / (int)sizeof(Tb);
     const int t = threadIdx.x;
     const int warp = t >> 5;
     const int K2 = ka + kb;
@@ -154,6 +156,21 @@ k_gram_tc(int64_t n, const Ta *__restrict__ A, int lda, int ka, const Tb *__rest
     bool fresh = true;  // next MMA overwrites the accumulator
     bool ok = true;
     const int64_t ntiles = (n + TC_TILE - 1) / TC_TILE;
+    // the 16-byte chunks of one tile held by this thread (loaded one tile ahead)
+    uint4 buf[TC_MAXQ];
+    auto load_tile = [&](int64_t tl) {
+        if (tl >= ntiles) return;
+        const int64_t q0 = tl * TC_TILE;
+        const int rws = (int)(n - q0 < TC_TILE ? n - q0 : TC_TILE);
+        const int na = rws * lda / EA, nb = rws * ldb / EB;
+#pragma unroll
+        for (int u = 0; u < TC_MAXQ; ++u) {
+            const int q = t + u * TC_THREADS;
+            if (q < na) buf[u] = __ldg(reinterpret_cast<const uint4 *>(A + q0 * lda) + q);
+            else if (q - na < nb) buf[u] = __ldg(reinterpret_cast<const uint4 *>(B + q0 * ldb) + (q - na));
+        }
+    };
+    load_tile(blockIdx.x);
     int it = 0;
     for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it) {
         const int st = it & 1;
@@ -163,21 +180,49 @@ k_gram_tc(int64_t n, const Ta *__restrict__ A, int lda, int ka, const Tb *__rest
             pending[st] = false;
             if (!ok) break;
         }
-        // ---- stage: row r0 + t of the tile, split into S BF16 pieces, K-major core matrices
-        const int64_t r = tile * TC_TILE + t;
-        unsigned char *base = sm.stage[st] + (t >> 4) * TC_SLICE_BYTES;
-        const int kk = t & 15;
-        const int kofs = (kk >> 3) * 128 + (kk & 7) * 2;
-        for (int c = 0; c < K2; ++c) {
-            float x = 0.f;
-            if (r < n) x = c < ka ? cvt<float>(A[r * lda + c]) : cvt<float>(B[r * ldb + (c - ka)]);
+        // ---- stage: the tile's rows of A and B are contiguous (row stride lda / ldb), so the
+        // CTA reads them as 16-byte chunks in address order (all loads issued first), then each
+        // element is split into S BF16 pieces written into the K-major core-matrix layout
+        const int64_t r0 = tile * TC_TILE;
+        const int rows = (int)(n - r0 < TC_TILE ? n - r0 : TC_TILE);
+        const int qa = rows * lda / EA, qb = rows * ldb / EB;  // chunks of A and of B
 #pragma unroll
-            for (int s = 0; s < S; ++s) {
-                const __nv_bfloat16 h = __float2bfloat16_rn(x);
-                x -= __bfloat162float(h);
-                const int m = s * K2 + c;
-                *reinterpret_cast<__nv_bfloat16 *>(base + ((m >> 3) * 2) * 128 + (m & 7) * 16 +
-                                                   kofs) = h;
+        for (int u = 0; u < TC_MAXQ; ++u) {
+            const int q = t + u * TC_THREADS;
+            const bool in_a = q < qa;
+            if (!in_a && q - qa >= qb) continue;
+            const int e0 = in_a ? q * EA : (q - qa) * EB;
+            const int ld = in_a ? lda : ldb;
+            const int row = e0 / ld, col0 = e0 - row * ld;
+            unsigned char *base = sm.stage[st] + (row >> 4) * TC_SLICE_BYTES;
+            const int kk = row & 15;
+            const int kofs = (kk >> 3) * 128 + (kk & 7) * 2;
+            const int ne = in_a ? EA : EB;
+            for (int e = 0; e < ne; ++e) {
+                const int col = col0 + e;
+                if (col >= (in_a ? ka : kb)) break;
+                float x = in_a ? cvt<float>(reinterpret_cast<const Ta *>(&buf[u])[e])
+                               : cvt<float>(reinterpret_cast<const Tb *>(&buf[u])[e]);
+                const int c = in_a ? col : ka + col;
+#pragma unroll
+                for (int s = 0; s < S; ++s) {
+                    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+                    x -= __bfloat162float(h);
+                    const int m = s * K2 + c;
+                    *reinterpret_cast<__nv_bfloat16 *>(base + ((m >> 3) * 2) * 128 +
+                                                       (m & 7) * 16 + kofs) = h;
+                }
+            }
+        }
+        load_tile(tile + gridDim.x);  // next tile's chunks fly during the MMA and the fold
+        if (rows < TC_TILE) {  // tail tile: zero the rows past the end (all pieces)
+            for (int e = t; e < (TC_TILE - rows) * S * K2; e += TC_THREADS) {
+                const int row = rows + e / (S * K2), m = e % (S * K2);
+                const int kk = row & 15;
+                *reinterpret_cast<__nv_bfloat16 *>(sm.stage[st] + (row >> 4) * TC_SLICE_BYTES +
+                                                   ((m >> 3) * 2) * 128 + (m & 7) * 16 +
+                                                   (kk >> 3) * 128 + (kk & 7) * 2) =
+                    __float2bfloat16_rn(0.f);
             }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -202,10 +247,12 @@ k_gram_tc(int64_t n, const Ta *__restrict__ A, int lda, int ka, const Tb *__rest
             pending[st] = false;
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;");
+            // warp w reads lane quarter w % 4 (its own TMEM lanes), column half w / 4
+            const int lane_m = (warp & 3) * 32 + (t & 31);
 #pragma unroll 1
-            for (int c0 = 0; c0 < TC_COLS; c0 += 32) {
+            for (int c0 = (warp >> 2) * (TC_COLS / 2); c0 < ((warp >> 2) + 1) * (TC_COLS / 2); c0 += 32) {
                 uint32_t v[32];
-                const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+                const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)c0;
                 asm volatile(
                     "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
                     "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
@@ -220,7 +267,7 @@ k_gram_tc(int64_t n, const Ta *__restrict__ A, int lda, int ka, const Tb *__rest
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
                 for (int q = 0; q < 32; ++q) {
-                    const int idx = (c0 + q) * 128 + t;  // [n][m], m = this thread's lane
+                    const int idx = (c0 + q) * 128 + lane_m;  // [n][m], m = this thread's lane
                     float s = sm.acc_hi[idx], e = sm.acc_lo[idx];
                     two_sum(s, e, __uint_as_float(v[q]));
                     sm.acc_hi[idx] = s;
@@ -282,10 +329,13 @@ static int tc_ctas(int64_t n) {
 }
 
 // pieces per value for the tensor path, 0 when it does not apply
-int gram_tc_pieces(sped_dtype at, sped_dtype bt, int ka, int kb) {
+int gram_tc_pieces(sped_dtype at, sped_dtype bt, int ka, int kb, int lda, int ldb) {
     const bool a_ok = at == SPED_F32 || at == SPED_BF16;
     const bool b_ok = kb == 0 || bt == SPED_F32 || bt == SPED_BF16;
     if (!a_ok || !b_ok) return 0;
+    // every thread holds at most TC_MAXQ 16-byte chunks of a tile
+    const int ea = 16 / (int)dtype_size(at), eb = kb ? 16 / (int)dtype_size(bt) : 1;
+    if (TC_TILE * (lda / ea + (kb ? ldb / eb : 0)) > TC_MAXQ * TC_THREADS) return 0;
     const int S = (at == SPED_F32 || (kb > 0 && bt == SPED_F32)) ? 3 : 1;
     return S * (ka + kb) <= 128 ? S : 0;
 }
@@ -316,15 +366,15 @@ using bf16 = __nv_bfloat16;
 sped_status launch_gram_tc(int64_t n, const void *A, sped_dtype at, int lda, int ka, const void *B,
                            sped_dtype bt, int ldb, int kb, double *G, Scratch &scr,
                            cudaStream_t st) {
-    const int S = gram_tc_pieces(at, bt, ka, kb);
+    const int S = gram_tc_pieces(at, bt, ka, kb, lda, kb ? ldb : 0);
     if (!S) return fail(SPED_ERR_UNSUPPORTED, "gram (tensor path): not applicable");
     const int ctas = tc_ctas(n);
     double *partial = (double *)scr.take(sizeof(double) * (size_t)(ka + kb) * (ka + kb) * ctas);
     if (!partial) return fail(SPED_ERR_SCRATCH, "gram (tensor path): scratch too small");
-    if (kb == 0) {
+    if (kb == 0) {  // no B columns: no B chunks are read
         B = A;
         bt = at;
-        ldb = lda;
+        ldb = 0;
     }
     if (S == 3) {
         if (at == SPED_F32 && bt == SPED_F32) return run_tc<float, float, 3>(n, A, lda, ka, B, ldb, kb, G, partial, ctas, st);

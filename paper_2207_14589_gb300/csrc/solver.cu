@@ -159,23 +159,31 @@ k_small(const double *__restrict__ G, int k, double eta, int solver, Coefs *cf, 
     if (t == 0 && bad) atomicOr(&cf->err, SOLVE_ERR_NOT_PD);
 }
 
-// V <- (V A + Y B) diag(scale), in place, one row per thread. Accumulates, per column,
+// V <- (V A + Y B) diag(scale), in place, one row per thread. The coefficient matrices sit in
+// shared memory as [j][i] with i contiguous, so one 16-byte shared load feeds four outputs;
+// B is diagonal for mu-EG (bdiag), which skips its k^2 products. The row is held in registers,
+// so each group of four outputs is stored as soon as it is computed. Accumulates, per column,
 // ||v_new_i - v_i||^2 and the invariant-subspace residual ||y_i - V C_i||^2 (old V).
 template <typename Tm, typename Ty, int KM>
 __global__ void __launch_bounds__(256)
 k_update(int64_t n, Tm *__restrict__ V, int ldv, const Ty *__restrict__ Y, int ldy, int k,
-         Coefs *cf) {
+         Coefs *cf, int bdiag) {
     using A = typename AccOf<Tm>::type;
-    __shared__ A sA[KM * KM], sB[KM * KM], sC[KM * KM], sS[KM];
+    static_assert(KM % 4 == 0, "KM");
+    __shared__ __align__(16) A sA[KM * KM];
+    __shared__ __align__(16) A sB[KM * KM];
+    __shared__ __align__(16) A sC[KM * KM];
+    __shared__ A sS[KM];
     __shared__ double sdv[KM], sres[KM];
     for (int e = threadIdx.x; e < KM * KM; e += blockDim.x) {
-        int j = e / KM, i = e % KM;
-        sA[e] = (A)cf->A[j * MAXK + i];
-        sB[e] = (A)cf->B[j * MAXK + i];
-        sC[e] = (A)cf->C[j * MAXK + i];
+        const int j = e / KM, i = e % KM;
+        const bool in = i < k && j < k;
+        sA[e] = in ? (A)cf->A[j * MAXK + i] : A(0);
+        sB[e] = in ? (A)cf->B[j * MAXK + i] : A(0);
+        sC[e] = in ? (A)cf->C[j * MAXK + i] : A(0);
     }
     for (int e = threadIdx.x; e < KM; e += blockDim.x) {
-        sS[e] = (A)cf->scale[e];
+        sS[e] = e < k ? (A)cf->scale[e] : A(0);
         sdv[e] = 0.0;
         sres[e] = 0.0;
     }
@@ -188,29 +196,42 @@ k_update(int64_t n, Tm *__restrict__ V, int ldv, const Ty *__restrict__ Y, int l
     }
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n;
          r += (int64_t)gridDim.x * blockDim.x) {
-        A v[KM], y[KM];
         Tm *vr = V + r * ldv;
         const Ty *yr = Y + r * ldy;
+        A v[KM], y[KM];
 #pragma unroll
         for (int j = 0; j < KM; ++j) {
             v[j] = j < k ? cvt<A>(vr[j]) : A(0);
             y[j] = j < k ? cvt<A>(__ldg(yr + j)) : A(0);
         }
 #pragma unroll
-        for (int i = 0; i < KM; ++i) {
-            if (i < k) {
-                A s = A(0), p = A(0);
+        for (int i0 = 0; i0 < KM; i0 += 4) {
+            if (i0 >= k) break;
+            A s[4] = {A(0), A(0), A(0), A(0)}, pq[4] = {A(0), A(0), A(0), A(0)};
 #pragma unroll
-                for (int j = 0; j < KM; ++j) {
-                    s += v[j] * sA[j * KM + i] + y[j] * sB[j * KM + i];
-                    p += v[j] * sC[j * KM + i];
+            for (int j = 0; j < KM; ++j) {
+                const A *a4 = sA + j * KM + i0, *c4 = sC + j * KM + i0;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    s[q] += v[j] * a4[q];
+                    pq[q] += v[j] * c4[q];
                 }
-                s *= sS[i];
-                A d = s - v[i];
+                if (!bdiag) {
+                    const A *b4 = sB + j * KM + i0;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) s[q] += y[j] * b4[q];
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int i = i0 + q;
+                if (bdiag) s[q] += y[i] * sB[i * KM + i];
+                s[q] *= sS[i];
+                const A d = s[q] - v[i];
                 dv[i] += d * d;
-                A q = y[i] - p;
-                rs[i] += q * q;
-                vr[i] = from_acc<Tm>(s);
+                const A e = y[i] - pq[q];
+                rs[i] += e * e;
+                if (i < k) vr[i] = from_acc<Tm>(s[q]);
             }
         }
     }
@@ -251,13 +272,17 @@ __global__ void k_rayleigh_out(const double *G, int k, double *out) {
 
 template <typename Tm, typename Ty>
 static sped_status run_update(int64_t n, void *V, int ldv, const void *Y, int ldy, int k,
-                              Coefs *cf, cudaStream_t st) {
-    int blocks = 2 * device_sm_count() * 4;
-    int64_t need = (n + 255) / 256;
+                              Coefs *cf, int bdiag, cudaStream_t st) {
+    int blocks = device_sm_count() * 4;
+    const int64_t need = (n + 255) / 256;
     if (need < blocks) blocks = (int)(need > 0 ? need : 1);
-    if (k <= 8) k_update<Tm, Ty, 8><<<blocks, 256, 0, st>>>(n, (Tm *)V, ldv, (const Ty *)Y, ldy, k, cf);
-    else if (k <= 16) k_update<Tm, Ty, 16><<<blocks, 256, 0, st>>>(n, (Tm *)V, ldv, (const Ty *)Y, ldy, k, cf);
-    else k_update<Tm, Ty, 32><<<blocks, 256, 0, st>>>(n, (Tm *)V, ldv, (const Ty *)Y, ldy, k, cf);
+#define UPD(KMV) k_update<Tm, Ty, KMV><<<blocks, 256, 0, st>>>(n, (Tm *)V, ldv, (const Ty *)Y, ldy, k, cf, bdiag)
+    if (k <= 8) UPD(8);
+    else if (k <= 16) UPD(16);
+    else if (k <= 20) UPD(20);
+    else if (k <= 24) UPD(24);
+    else UPD(32);
+#undef UPD
     SPED_CHECK_LAUNCH("k_update");
     return SPED_OK;
 }
@@ -322,10 +347,11 @@ static sped_status eig_step_impl(const sped_graph *g, const sped_step_opts *o, v
     SPED_CUDA(cudaMemsetAsync(&cf->err, 0, sizeof(int), st));
     k_small<<<1, SMALL_THREADS, 0, st>>>(G, k, o->eta, (int)o->solver, cf, d_stats);
     SPED_CHECK_LAUNCH("k_small");
-    if (vt == SPED_F32 && o->y_t == SPED_F32) SPED_TRY((run_update<float, float>(g->n, V, ld, Y, L.ldy, k, cf, st)));
-    else if (vt == SPED_F32 && o->y_t == SPED_F64) SPED_TRY((run_update<float, double>(g->n, V, ld, Y, L.ldy, k, cf, st)));
-    else if (vt == SPED_F64 && o->y_t == SPED_F64) SPED_TRY((run_update<double, double>(g->n, V, ld, Y, L.ldy, k, cf, st)));
-    else if (vt == SPED_F64 && o->y_t == SPED_F32) SPED_TRY((run_update<double, float>(g->n, V, ld, Y, L.ldy, k, cf, st)));
+    const int bdiag = o->solver == SPED_SOLVER_MU_EG;  // mu-EG: Y enters through eta I
+    if (vt == SPED_F32 && o->y_t == SPED_F32) SPED_TRY((run_update<float, float>(g->n, V, ld, Y, L.ldy, k, cf, bdiag, st)));
+    else if (vt == SPED_F32 && o->y_t == SPED_F64) SPED_TRY((run_update<float, double>(g->n, V, ld, Y, L.ldy, k, cf, bdiag, st)));
+    else if (vt == SPED_F64 && o->y_t == SPED_F64) SPED_TRY((run_update<double, double>(g->n, V, ld, Y, L.ldy, k, cf, bdiag, st)));
+    else if (vt == SPED_F64 && o->y_t == SPED_F32) SPED_TRY((run_update<double, float>(g->n, V, ld, Y, L.ldy, k, cf, bdiag, st)));
     else return fail(SPED_ERR_UNSUPPORTED, "eig_step: master V must be F32 or F64");
     if (d_stats) {
         k_finish_stats<<<1, MAXK, 0, st>>>(k, cf, d_stats);

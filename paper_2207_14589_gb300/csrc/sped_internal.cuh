@@ -281,7 +281,7 @@ size_t poly_step_scratch(const sped_graph *g, int k, sped_dtype xt, int split);
 sped_status launch_gram(int64_t n, const void *A, sped_dtype at, int lda, int ka, const void *B,
                         sped_dtype bt, int ldb, int kb, double *G, Scratch &scr, cudaStream_t st);
 size_t gram_scratch(int64_t n, int ka, int kb);
-int gram_tc_pieces(sped_dtype at, sped_dtype bt, int ka, int kb);
+int gram_tc_pieces(sped_dtype at, sped_dtype bt, int ka, int kb, int lda, int ldb);
 size_t gram_tc_scratch(int64_t n, int ka, int kb);
 sped_status launch_gram_tc(int64_t n, const void *A, sped_dtype at, int lda, int ka, const void *B,
                            sped_dtype bt, int ldb, int kb, double *G, Scratch &scr,

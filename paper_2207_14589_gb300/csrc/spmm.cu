@@ -429,132 +429,6 @@ sped_status launch_poly_step(const sped_graph *g, int k, const void *X, sped_dty
 }
 
 // ---------------------------------------------------------------------------------------
-// line-packed BF16 chain buffers
-// ---------------------------------------------------------------------------------------
-// The intermediate products of a BF16 chain live in library scratch, so their layout is
-// free: whole rows are packed into 128-byte lines, row j at byte (j / R) * 128 + (j % R) * rb
-// with rb = 8 ceil(k / 4) (four elements per 8-byte lane chunk) and R = floor(128 / rb). No
-// gathered row then straddles two lines (dense 48-byte rows of k = 20 straddle in 3 of 8
-// rows), which is what the random gathers of the chain step are limited by.
-struct Packed {
-    unsigned char *base;
-    int rb;          // bytes per row
-    int rpl;         // rows per 128-byte line (>= 2)
-    uint32_t magic;  // ceil(2^32 / rpl): j / rpl = umulhi(j, magic) for j < 2^32 / rpl
-};
-
-__device__ __forceinline__ int64_t packed_off(const Packed &P, int64_t j) {
-    const uint32_t q = __umulhi((uint32_t)j, P.magic);
-    return (int64_t)q * 128 + (int64_t)((uint32_t)j - q * (uint32_t)P.rpl) * P.rb;
-}
-
-static Packed packed_layout(void *base, int k) {
-    Packed P;
-    P.base = (unsigned char *)base;
-    P.rb = 8 * ((k + 3) / 4);
-    P.rpl = 128 / P.rb;
-    P.magic = (uint32_t)((0x100000000ULL + P.rpl - 1) / P.rpl);
-    return P;
-}
-
-static size_t packed_bytes(int64_t n, int k) {
-    const int rb = 8 * ((k + 3) / 4), rpl = 128 / rb;
-    return (size_t)((n + rpl - 1) / rpl) * 128;
-}
-
-// Same arithmetic as k_step_rowgroup with four elements per lane: X is packed BF16 (XP) or a
-// dense block of Tx, Y is packed BF16 (YP) or a dense block of Ty; V (Horner term) is dense F32.
-template <bool XP, bool YP, typename Tx, typename Ty, bool W, bool HV>
-__global__ void __launch_bounds__(STEP_THREADS)
-k_step_packed(int n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
-              const float *__restrict__ w, Packed PX, const Tx *__restrict__ X, int ldx, Packed PY,
-              Ty *__restrict__ Y, int ldy, const float *__restrict__ V, int ldv, int k, int C,
-              int rows_per_warp, float alpha, float beta, float gamma) {
-    constexpr int E = 4;
-    using XT = typename std::conditional<XP, __nv_bfloat16, Tx>::type;
-    using YT = typename std::conditional<YP, __nv_bfloat16, Ty>::type;
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = ((int64_t)blockIdx.x * STEP_THREADS + threadIdx.x) >> 5;
-    const int rw = lane / C;
-    const int c = lane - rw * C;
-    if (rw >= rows_per_warp) return;
-    const int64_t r = warp * rows_per_warp + rw;
-    if (r >= n) return;
-    auto xrow = [&](int64_t j) -> const XT * {
-        if constexpr (XP) return reinterpret_cast<const XT *>(PX.base + packed_off(PX, j)) + c * E;
-        else return reinterpret_cast<const XT *>(X) + j * ldx + c * E;
-    };
-    const int p0 = __ldg(rp + r), p1 = __ldg(rp + r + 1);
-    float acc[E] = {0.f, 0.f, 0.f, 0.f};
-    float dsum = 0.f;
-    int p = p0;
-    for (; p + UNROLL <= p1; p += UNROLL) {
-        int j[UNROLL];
-#pragma unroll
-        for (int u = 0; u < UNROLL; ++u) j[u] = __ldg(ci + p + u);
-        float x[UNROLL][E];
-#pragma unroll
-        for (int u = 0; u < UNROLL; ++u) load_chunk<XT, E, float>(xrow(j[u]), x[u]);
-#pragma unroll
-        for (int u = 0; u < UNROLL; ++u) {
-            const float wu = W ? __ldg(w + p + u) : 1.f;
-            dsum += wu;
-#pragma unroll
-            for (int i = 0; i < E; ++i) acc[i] += W ? wu * x[u][i] : x[u][i];
-        }
-    }
-    for (; p < p1; ++p) {
-        const int j = __ldg(ci + p);
-        float x[E];
-        load_chunk<XT, E, float>(xrow(j), x);
-        const float wu = W ? __ldg(w + p) : 1.f;
-        dsum += wu;
-#pragma unroll
-        for (int i = 0; i < E; ++i) acc[i] += W ? wu * x[i] : x[i];
-    }
-    float xr[E], out[E];
-    load_chunk<XT, E, float>(xrow(r), xr);
-#pragma unroll
-    for (int i = 0; i < E; ++i) out[i] = gamma * xr[i] + beta * (dsum * xr[i] - acc[i]);
-    const int rem = k - c * E;
-    if constexpr (HV) {
-        float vr[E];
-        if (rem >= E) load_chunk<float, E, float>(V + r * ldv + c * E, vr);
-        else load_partial<float, E, float>(V + r * ldv + c * E, rem, vr);
-#pragma unroll
-        for (int i = 0; i < E; ++i) out[i] += alpha * vr[i];
-    }
-    if constexpr (YP) {
-        store_chunk<YT, E, float>(reinterpret_cast<YT *>(PY.base + packed_off(PY, r)) + c * E, out);
-    } else {
-        YT *yr = reinterpret_cast<YT *>(Y) + r * ldy + c * E;
-        if (rem >= E) store_chunk<YT, E, float>(yr, out);
-        else store_partial<YT, E, float>(yr, rem, out);
-    }
-}
-
-template <bool XP, bool YP, typename Tx, typename Ty>
-static sped_status run_packed(const sped_graph *g, int k, Packed PX, const void *X, int ldx,
-                              Packed PY, void *Y, int ldy, const float *V, int ldv, double al,
-                              double be, double ga, cudaStream_t st) {
-    const int C = (k + 3) / 4;
-    const int per_warp = 32 / C;
-    const int64_t warps = (g->n + per_warp - 1) / per_warp;
-    const int64_t blocks = (warps * 32 + STEP_THREADS - 1) / STEP_THREADS;
-    if (blocks == 0) return SPED_OK;
-    const bool W = g->w != nullptr, HV = V != nullptr && al != 0.0;
-#define PK(WW, HH)                                                                             \
-    k_step_packed<XP, YP, Tx, Ty, WW, HH><<<(unsigned)blocks, STEP_THREADS, 0, st>>>(          \
-        (int)g->n, g->rp, g->ci, g->w, PX, (const Tx *)X, ldx, PY, (Ty *)Y, ldy, V, ldv, k, C, \
-        per_warp, (float)al, (float)be, (float)ga)
-    if (W) { if (HV) PK(true, true); else PK(true, false); }
-    else { if (HV) PK(false, true); else PK(false, false); }
-#undef PK
-    SPED_CHECK_LAUNCH("k_step_packed");
-    return SPED_OK;
-}
-
-// ---------------------------------------------------------------------------------------
 // exact p(L) V: the chain of steps for the graph's polynomial
 // ---------------------------------------------------------------------------------------
 struct StepCoef {
@@ -583,10 +457,6 @@ size_t apply_poly_scratch(const sped_graph *g, int k, sped_dtype ct, sped_mode m
     int steps = (int)chain_coefs(g->poly).size();
     ScratchPlan p;
     size_t buf = (size_t)g->n * padded_ld(k, ct) * dtype_size(ct);
-    if (ct == SPED_BF16 && k <= 32) {
-        const size_t pk = packed_bytes(g->n, k);
-        if (pk > buf) buf = pk;
-    }
     if (steps >= 2) p.add(buf);
     if (steps >= 3) p.add(buf);
     size_t ms = 0;
@@ -606,11 +476,7 @@ sped_status apply_poly_impl(const sped_graph *g, int k, const void *V, sped_dtyp
     std::vector<StepCoef> cs = chain_coefs(g->poly);
     const int steps = (int)cs.size();
     const int ldc = padded_ld(k, ct);
-    // BF16 chains on the row-group schedule keep their intermediate products line-packed
-    const bool packed = ct == SPED_BF16 && k <= 32 && steps >= 2 && vt == SPED_F32 &&
-                        (yt == SPED_F32 || yt == SPED_BF16) && !use_merge(g, 0) &&
-                        g->n < (int64_t)(0x100000000LL / (128 / (8 * ((k + 3) / 4))));
-    const size_t buf = packed ? packed_bytes(g->n, k) : (size_t)g->n * ldc * dtype_size(ct);
+    const size_t buf = (size_t)g->n * ldc * dtype_size(ct);
     void *b[2] = {nullptr, nullptr};
     if (steps >= 2) b[0] = scr.take(buf);
     if (steps >= 3) b[1] = scr.take(buf);
@@ -620,31 +486,6 @@ sped_status apply_poly_impl(const sped_graph *g, int k, const void *V, sped_dtyp
     const size_t off = align_up(scr.used, 256);
     const size_t rest = (scr.base != nullptr && off < scr.cap) ? scr.cap - off : 0;
     Scratch step_scr(rest ? scr.base + off : nullptr, rest);
-    if (packed) {
-        const Packed P0 = packed_layout(b[0], k), P1 = packed_layout(b[1], k), none{};
-        const Packed Pb[2] = {P0, P1};
-        for (int t = 0; t < steps; ++t) {
-            const StepCoef &q = cs[t];
-            const float *Vh = q.uses_v ? (const float *)V : nullptr;
-            if (t == 0) {
-                SPED_TRY((run_packed<false, true, float, __nv_bfloat16>(
-                    g, k, none, V, ldv, Pb[0], nullptr, 0, Vh, ldv, q.alpha, q.beta, q.gamma, st)));
-            } else if (t < steps - 1) {
-                SPED_TRY((run_packed<true, true, __nv_bfloat16, __nv_bfloat16>(
-                    g, k, Pb[(t - 1) % 2], nullptr, 0, Pb[t % 2], nullptr, 0, Vh, ldv, q.alpha,
-                    q.beta, q.gamma, st)));
-            } else if (yt == SPED_F32) {
-                SPED_TRY((run_packed<true, false, __nv_bfloat16, float>(
-                    g, k, Pb[(t - 1) % 2], nullptr, 0, none, Y, ldy, Vh, ldv, q.alpha, q.beta,
-                    q.gamma, st)));
-            } else {
-                SPED_TRY((run_packed<true, false, __nv_bfloat16, __nv_bfloat16>(
-                    g, k, Pb[(t - 1) % 2], nullptr, 0, none, Y, ldy, Vh, ldv, q.alpha, q.beta,
-                    q.gamma, st)));
-            }
-        }
-        return SPED_OK;
-    }
     for (int t = 0; t < steps; ++t) {
         const void *x = t == 0 ? V : b[(t - 1) % 2];
         sped_dtype xt = t == 0 ? vt : ct;
