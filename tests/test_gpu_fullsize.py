@@ -1,0 +1,81 @@
+"""Parity at the benchmark's full size and launch configuration: the stochastic block model with
+N = 1,000,000 nodes in 20 blocks, mean degree 16, k = 20, limit form of degree 41, BF16 chain with
+F32 master. Sampled output rows are recomputed one by one by the oracle; whole-size results
+are checked against the oracle where it finishes in tens of seconds, or against properties that
+hold at any size."""
+import numpy as np
+import pytest
+import torch
+
+import gen
+import oracle
+import paper_2207_14589_gb300 as sped
+from util_gpu import DEV, host, rel, stored, to_block
+
+pytestmark = pytest.mark.gpu
+
+N, BLOCKS, K, ELL = 1_000_000, 20, 20, 41
+
+
+@pytest.fixture(scope="module")
+def cfg2():
+    g = gen.sbm(N, BLOCKS, 14 / 49_999, 2 / 950_000, seed=gen.DEFAULT_SEED)
+    G = sped.Graph.from_csr(g)
+    info = G.set_polynomial(sped.POLY_LIMIT_EXP, ELL)
+    return g, G, info
+
+
+def test_chain_step_sampled_rows(cfg2):
+    g, G, info = cfg2
+    s = info.scale_s
+    X0 = gen.gaussian_block(N, K, seed=3)
+    X = to_block(X0, torch.bfloat16)
+    Y = sped.alloc_block(N, K, torch.float32, DEV)
+    sped.poly_step(G, X, Y, K, alpha=0.0, beta=-s, gamma=1.0)
+    torch.cuda.synchronize()
+    Xs = stored(X0, torch.bfloat16)
+    rows = np.random.default_rng(0).choice(N, size=3000, replace=False)
+    got = Y[torch.from_numpy(rows).to(DEV), :K].double().cpu().numpy()
+    want = np.empty((len(rows), K))
+    for t, r in enumerate(rows):  # one row at a time: x_r - s (d_r x_r - sum_j x_j)
+        nb = g.col_idx[g.row_ptr[r]:g.row_ptr[r + 1]]
+        want[t] = Xs[r] - s * (len(nb) * Xs[r] - Xs[nb].sum(axis=0))
+    assert rel(got, want) <= 1e-5
+
+
+def test_chain_keeps_constant_vector(cfg2):
+    # L 1 = 0, so every step maps 1 to 1 exactly (BF16 storage, F32 accumulation)
+    g, G, info = cfg2
+    V = to_block(np.ones((N, K)), torch.float32)
+    Y = sped.alloc_block(N, K, torch.float32, DEV)
+    sped.apply_poly(G, V, Y, K, chain_dtype=torch.bfloat16)
+    torch.cuda.synchronize()
+    assert torch.all(Y[:, :K] == 1.0)
+
+
+def test_tensor_gram_full_size():
+    A0 = gen.gaussian_block(N, K, seed=5)
+    B0 = gen.gaussian_block(N, K, seed=6) * 0.01
+    A, B = to_block(A0, torch.float32), to_block(B0, torch.float32)
+    Gm = sped.gram(A, K, B, K).cpu().numpy()
+    M = np.concatenate([stored(A0, torch.float32), stored(B0, torch.float32)], axis=1)
+    assert rel(Gm, M.T @ M) <= 2e-6
+
+
+def test_mixed_eig_step_full_size(cfg2):
+    # one benchmark step (BF16 chain, F32 master, mu-EG eta = 1) against the oracle's FP64 step
+    g, G, info = cfg2
+    V0 = gen.gaussian_block(N, K, seed=7)
+    V0 /= np.linalg.norm(V0, axis=0)
+    V = to_block(V0, torch.float32)
+    opts = sped.step_opts(sped.MU_EG, 1.0, torch.bfloat16, torch.float32)
+    sped.eig_step(G, V, K, opts)
+    torch.cuda.synchronize()
+    Vs = stored(V0, torch.float32)
+    Y = oracle.poly_limit(g, Vs, info.scale_s, ELL)
+    want = oracle.mu_eg_step(Vs, Y, 1.0)
+    tol = 1e-2  # BF16 storage bound on p(L) V, carried through the step (gain measured below)
+    D = np.random.default_rng(1).standard_normal(Y.shape)
+    Yp = Y + tol * np.linalg.norm(Y) * D / np.linalg.norm(D)
+    gain = rel(oracle.mu_eg_step(Vs, Yp, 1.0), want) / tol
+    assert rel(host(V, K), want) <= 1.5 * tol * max(1.0, gain)
