@@ -14,8 +14,9 @@
 
 namespace sped {
 
-constexpr int SMALL_THREADS = 128;
+constexpr int SMALL_THREADS = 256;
 constexpr int MAXK = 32;
+constexpr int SLD = MAXK + 1;  // row stride of the k x k work arrays (odd: conflict-free columns)
 
 enum : int { SOLVE_ERR_NOT_PD = 1, SOLVE_ERR_NAN = 2 };
 
@@ -30,25 +31,60 @@ struct Coefs {
     int err;
 };
 
-// Upper Cholesky factor R (R^T R = M) of a k x k matrix given by an accessor, in shared memory;
-// sets *bad when a pivot is not positive. All threads of the block take part.
-template <typename F>
-__device__ void chol_upper(F Mf, double *R, int k, int *bad) {
+// The k x k stage is FP64 and latency-bound on one SM, so every kernel-level step below spreads
+// its products over all threads and keeps the serial chain short: one rsqrt per Cholesky pivot,
+// divisions replaced by that reciprocal, one barrier per elimination step.
+
+// Right-looking Cholesky W = R^T R of a symmetric k x k array (upper triangle read, W
+// overwritten), R upper in R[j*SLD + i] (i >= j), rinv[j] = 1 / R_jj. Sets *bad on a pivot
+// that is not positive (that pivot is replaced by 1 so the rest stays finite).
+__device__ void chol_rl(double *W, double *R, double *rinv, int k, int *bad) {
+    const int t = threadIdx.x, nt = blockDim.x;
     for (int j = 0; j < k; ++j) {
-        if (threadIdx.x == 0) {
-            double d = Mf(j, j);
-            for (int p = 0; p < j; ++p) d -= R[p * MAXK + j] * R[p * MAXK + j];
-            if (!(d > 0.0) || !isfinite(d)) {
-                *bad = 1;
-                d = 1.0;
-            }
-            R[j * MAXK + j] = sqrt(d);
+        const double d = W[j * SLD + j];
+        const bool ok = d > 0.0 && isfinite(d);
+        const double ri = ok ? rsqrt(d) : 1.0;
+        for (int i = j + t; i < k; i += nt) R[j * SLD + i] = i == j ? (ok ? d * ri : 1.0) : W[j * SLD + i] * ri;
+        if (t == 0) {
+            rinv[j] = ri;
+            if (!ok) *bad = 1;
+        }
+        const int m = k - 1 - j;
+        const double ri2 = ri * ri;
+        for (int e = t; e < m * m; e += nt) {
+            const int i = j + 1 + e / m, l = j + 1 + e % m;
+            if (l >= i) W[i * SLD + l] -= W[j * SLD + i] * W[j * SLD + l] * ri2;
         }
         __syncthreads();
-        for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x) {
-            double s = Mf(j, i);
-            for (int p = 0; p < j; ++p) s -= R[p * MAXK + j] * R[p * MAXK + i];
-            R[j * MAXK + i] = s / R[j * MAXK + j];
+    }
+}
+
+// Forward substitution R^T Z = B for nrhs right-hand sides (B[j*SLD + c]); B is consumed.
+__device__ void trsv_upper_t(const double *R, const double *rinv, double *B, double *Z, int k,
+                             int nrhs) {
+    const int t = threadIdx.x, nt = blockDim.x;
+    for (int j = 0; j < k; ++j) {
+        const double ri = rinv[j];
+        for (int c = t; c < nrhs; c += nt) Z[j * SLD + c] = B[j * SLD + c] * ri;
+        const int m = k - 1 - j;
+        for (int e = t; e < m * nrhs; e += nt) {
+            const int i = j + 1 + e / nrhs, c = e % nrhs;
+            B[i * SLD + c] -= R[j * SLD + i] * (B[j * SLD + c] * ri);
+        }
+        __syncthreads();
+    }
+}
+
+// Back substitution R X = Z (Z consumed), X[j*SLD + c].
+__device__ void trsv_upper(const double *R, const double *rinv, double *Z, double *X, int k,
+                           int nrhs) {
+    const int t = threadIdx.x, nt = blockDim.x;
+    for (int j = k - 1; j >= 0; --j) {
+        const double ri = rinv[j];
+        for (int c = t; c < nrhs; c += nt) X[j * SLD + c] = Z[j * SLD + c] * ri;
+        for (int e = t; e < j * nrhs; e += nt) {
+            const int i = e / nrhs, c = e % nrhs;
+            Z[i * SLD + c] -= R[i * SLD + j] * (Z[j * SLD + c] * ri);
         }
         __syncthreads();
     }
@@ -57,21 +93,24 @@ __device__ void chol_upper(F Mf, double *R, int k, int *bad) {
 // k x k stage. G is (2k x 2k): [P H; H^T Q] with P = V^T V, H = V^T Y, Q = Y^T Y.
 __global__ void __launch_bounds__(SMALL_THREADS)
 k_small(const double *__restrict__ G, int k, double eta, int solver, Coefs *cf, double *stats) {
-    __shared__ double sG[2 * MAXK * 2 * MAXK];
-    __shared__ double R[MAXK * MAXK];
+    __shared__ double sP[MAXK * SLD], sH[MAXK * SLD], sW[MAXK * SLD], sR[MAXK * SLD],
+        sB[MAXK * SLD], rinv[MAXK], cmu[MAXK];
     __shared__ int bad, badp;
     const int K2 = 2 * k;
-    const int t = threadIdx.x;
-    for (int e = t; e < K2 * K2; e += blockDim.x) sG[e] = G[e];
+    const int t = threadIdx.x, nt = blockDim.x;
+    for (int e = t; e < k * k; e += nt) {
+        const int i = e / k, j = e % k;
+        sP[i * SLD + j] = G[i * K2 + j];
+        sH[i * SLD + j] = G[i * K2 + k + j];  // <v_i, y_j>
+    }
     if (t == 0) {
         bad = 0;
         badp = 0;
     }
-    for (int e = t; e < MAXK * MAXK; e += blockDim.x) {
+    for (int e = t; e < MAXK * MAXK; e += nt) {
         cf->A[e] = 0.0;
         cf->B[e] = 0.0;
         cf->C[e] = 0.0;
-        R[e] = 0.0;
     }
     if (t < MAXK) {
         cf->dv2[t] = 0.0;
@@ -80,99 +119,131 @@ k_small(const double *__restrict__ G, int k, double eta, int solver, Coefs *cf, 
         cf->ynorm[t] = 1.0;
     }
     __syncthreads();
-    auto P = [&](int i, int j) { return sG[i * K2 + j]; };
-    auto H = [&](int i, int j) { return sG[i * K2 + k + j]; };          // <v_i, y_j>
-    auto Q = [&](int i, int j) { return sG[(k + i) * K2 + k + j]; };    // <y_i, y_j>
     if (t < k) {
-        if (stats) stats[t] = H(t, t) / P(t, t);  // Rayleigh quotient of M
-        cf->ynorm[t] = sqrt(Q(t, t));
+        const double q = G[(k + t) * K2 + k + t];
+        if (stats) stats[t] = sH[t * SLD + t] / sP[t * SLD + t];  // Rayleigh quotient of M
+        cf->ynorm[t] = sqrt(q);
     }
-    // projection coefficients C = P^{-1} H (for the invariant-subspace residual)
-    chol_upper(P, R, k, &badp);
-    if (t < k && !badp) {
-        double z[MAXK];
-        for (int j = 0; j < k; ++j) {  // R^T z = H(:, t)
-            double s = H(j, t);
-            for (int p = 0; p < j; ++p) s -= R[p * MAXK + j] * z[p];
-            z[j] = s / R[j * MAXK + j];
-        }
-        for (int j = k - 1; j >= 0; --j) {  // R c = z
-            double s = z[j];
-            for (int p = j + 1; p < k; ++p) s -= R[j * MAXK + p] * z[p];
-            z[j] = s / R[j * MAXK + j];
-        }
-        for (int j = 0; j < k; ++j) cf->C[j * MAXK + t] = z[j];
-    }
-    __syncthreads();
     if (solver == SPED_SOLVER_MU_EG) {
+        // player i: u_i = sum_{j<=i} a_ij v_j + eta y_i with a_ij = -eta H_ij (j < i) and
+        // a_ii = 1 - eta c_i, c_i = H_ii - sum_{j<i} H_ij P_ij; ||u_i||^2 = a_i^T P a_i +
+        // 2 eta a_i^T H_{:,i} + eta^2 Q_ii. The a_i sit in sW (row i), T = a P in sB.
+        if (t < k) {
+            double c = sH[t * SLD + t];
+            for (int j = 0; j < t; ++j) c -= sH[t * SLD + j] * sP[t * SLD + j];
+            cmu[t] = c;
+        }
+        __syncthreads();
+        for (int e = t; e < k * k; e += nt) {
+            const int i = e / k, j = e % k;
+            sW[i * SLD + j] = j < i ? -eta * sH[i * SLD + j] : j == i ? 1.0 - eta * cmu[i] : 0.0;
+        }
+        __syncthreads();
+        for (int e = t; e < k * k; e += nt) {
+            const int i = e / k, j = e % k;
+            if (j <= i) {
+                double s = 0.0;
+                for (int l = 0; l <= i; ++l) s += sW[i * SLD + l] * sP[j * SLD + l];
+                sB[i * SLD + j] = s;
+            }
+        }
+        __syncthreads();
         if (t < k) {
             const int i = t;
-            double c = H(i, i);
-            for (int j = 0; j < i; ++j) c -= H(i, j) * P(i, j);
-            // u_i = sum_j a_j v_j + eta y_i with a_j = -eta H(i,j) (j<i), a_i = 1 - eta c
-            double a[MAXK];
-            for (int j = 0; j < k; ++j) a[j] = 0.0;
-            for (int j = 0; j < i; ++j) a[j] = -eta * H(i, j);
-            a[i] = 1.0 - eta * c;
-            double nrm = eta * eta * Q(i, i);
-            for (int j = 0; j <= i; ++j) {
-                double s = 0.0;
-                for (int l = 0; l <= i; ++l) s += a[l] * P(j, l);
-                nrm += a[j] * s + 2.0 * eta * a[j] * H(j, i);
-            }
-            for (int j = 0; j <= i; ++j) cf->A[j * MAXK + i] = a[j];
+            double nrm = eta * eta * G[(k + i) * K2 + k + i];
+            for (int j = 0; j <= i; ++j)
+                nrm += sW[i * SLD + j] * (sB[i * SLD + j] + 2.0 * eta * sH[j * SLD + i]);
+            for (int j = 0; j <= i; ++j) cf->A[j * MAXK + i] = sW[i * SLD + j];
             cf->B[i * MAXK + i] = eta;
             if (!(nrm > 0.0) || !isfinite(nrm)) {
                 atomicOr(&cf->err, SOLVE_ERR_NAN);
                 cf->scale[i] = 0.0;
             } else {
-                cf->scale[i] = 1.0 / sqrt(nrm);
+                cf->scale[i] = rsqrt(nrm);
             }
         }
-        return;
+        __syncthreads();
     }
+    // projection coefficients C = P^{-1} H (for the invariant-subspace residual; only when the
+    // caller asked for the step's statistics)
+    if (stats) {
+        for (int e = t; e < k * k; e += nt) {
+            const int i = e / k, j = e % k;
+            sW[i * SLD + j] = sP[i * SLD + j];
+            sB[i * SLD + j] = sH[i * SLD + j];
+        }
+        __syncthreads();
+        chol_rl(sW, sR, rinv, k, &badp);
+    }
+    if (stats && !badp) {
+        trsv_upper_t(sR, rinv, sB, sW, k, k);
+        trsv_upper(sR, rinv, sW, sB, k, k);
+        for (int e = t; e < k * k; e += nt) {
+            const int j = e / k, i = e % k;
+            cf->C[j * MAXK + i] = sB[j * SLD + i];
+        }
+    }
+    if (solver == SPED_SOLVER_MU_EG) return;
     // Oja: W = V + eta Y (eta <= 0: W = Y), Cholesky R^T R = W^T W, V <- W R^{-1}
     const bool pure = !(eta > 0.0);
-    auto Mw = [&](int i, int j) {
-        return pure ? Q(i, j) : P(i, j) + eta * (H(i, j) + H(j, i)) + eta * eta * Q(i, j);
-    };
-    for (int e = t; e < MAXK * MAXK; e += blockDim.x) R[e] = 0.0;
     __syncthreads();
-    chol_upper(Mw, R, k, &bad);
-    if (t < k) {
-        // column t of R^{-1} by back substitution
-        const int i = t;
-        double x[MAXK];
-        for (int j = 0; j < k; ++j) x[j] = 0.0;
-        x[i] = 1.0 / R[i * MAXK + i];
-        for (int j = i - 1; j >= 0; --j) {
-            double s = 0.0;
-            for (int p = j + 1; p <= i; ++p) s += R[j * MAXK + p] * x[p];
-            x[j] = -s / R[j * MAXK + j];
-        }
-        for (int j = 0; j <= i; ++j) {
-            cf->A[j * MAXK + i] = pure ? 0.0 : x[j];
-            cf->B[j * MAXK + i] = pure ? x[j] : eta * x[j];
-        }
-        cf->scale[i] = 1.0;
+    for (int e = t; e < k * k; e += nt) {
+        const int i = e / k, j = e % k;
+        const double q = G[(k + i) * K2 + k + j];
+        sW[i * SLD + j] = pure ? q : sP[i * SLD + j] + eta * (sH[i * SLD + j] + sH[j * SLD + i]) + eta * eta * q;
+        sB[i * SLD + j] = i == j ? 1.0 : 0.0;
     }
+    __syncthreads();
+    chol_rl(sW, sR, rinv, k, &bad);
+    trsv_upper(sR, rinv, sB, sW, k, k);  // sW = R^{-1}
+    for (int e = t; e < k * k; e += nt) {
+        const int j = e / k, i = e % k;
+        const double x = j <= i ? sW[j * SLD + i] : 0.0;
+        cf->A[j * MAXK + i] = pure ? 0.0 : x;
+        cf->B[j * MAXK + i] = pure ? x : eta * x;
+    }
+    if (t < k) cf->scale[t] = 1.0;
     if (t == 0 && bad) atomicOr(&cf->err, SOLVE_ERR_NOT_PD);
+}
+
+// One row of an N x k block into registers (zero past k): 16-byte loads when the row start and
+// the leading dimension allow it (vec), else element loads. Loads stop at the 16-byte chunk that
+// holds element k-1, which lies inside the row's leading dimension.
+template <int KM, bool RO, typename T, typename Acc>
+__device__ __forceinline__ void load_row(const T *p, int k, bool vec, Acc *out) {
+    constexpr int E = 16 / (int)sizeof(T);
+    static_assert(KM % E == 0, "row chunks");
+    if (vec) {
+#pragma unroll
+        for (int q = 0; q < KM / E; ++q) {
+            uint4 c = make_uint4(0, 0, 0, 0);
+            if (q * E < k) c = RO ? __ldg(reinterpret_cast<const uint4 *>(p) + q)
+                                  : reinterpret_cast<const uint4 *>(p)[q];
+            const T *e = reinterpret_cast<const T *>(&c);
+#pragma unroll
+            for (int u = 0; u < E; ++u) out[q * E + u] = q * E + u < k ? cvt<Acc>(e[u]) : Acc(0);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < KM; ++j) out[j] = j < k ? cvt<Acc>(RO ? __ldg(p + j) : p[j]) : Acc(0);
+    }
 }
 
 // V <- (V A + Y B) diag(scale), in place, one row per thread. The coefficient matrices sit in
 // shared memory as [j][i] with i contiguous, so one 16-byte shared load feeds four outputs;
 // B is diagonal for mu-EG (bdiag), which skips its k^2 products. The row is held in registers,
-// so each group of four outputs is stored as soon as it is computed. Accumulates, per column,
-// ||v_new_i - v_i||^2 and the invariant-subspace residual ||y_i - V C_i||^2 (old V).
-template <typename Tm, typename Ty, int KM>
+// so each group of four outputs is stored as soon as it is computed. With STATS it also
+// accumulates, per column, ||v_new_i - v_i||^2 and the invariant-subspace residual
+// ||y_i - V C_i||^2 (old V); without, it is the plain update (one read of V and Y, one write).
+template <typename Tm, typename Ty, int KM, bool STATS>
 __global__ void __launch_bounds__(256)
 k_update(int64_t n, Tm *__restrict__ V, int ldv, const Ty *__restrict__ Y, int ldy, int k,
-         Coefs *cf, int bdiag) {
+         Coefs *cf, int bdiag, int vec) {
     using A = typename AccOf<Tm>::type;
     static_assert(KM % 4 == 0, "KM");
     __shared__ __align__(16) A sA[KM * KM];
     __shared__ __align__(16) A sB[KM * KM];
-    __shared__ __align__(16) A sC[KM * KM];
+    __shared__ __align__(16) A sC[STATS ? KM * KM : 4];
     __shared__ A sS[KM];
     __shared__ double sdv[KM], sres[KM];
     for (int e = threadIdx.x; e < KM * KM; e += blockDim.x) {
@@ -180,7 +251,7 @@ k_update(int64_t n, Tm *__restrict__ V, int ldv, const Ty *__restrict__ Y, int l
         const bool in = i < k && j < k;
         sA[e] = in ? (A)cf->A[j * MAXK + i] : A(0);
         sB[e] = in ? (A)cf->B[j * MAXK + i] : A(0);
-        sC[e] = in ? (A)cf->C[j * MAXK + i] : A(0);
+        if (STATS) sC[e] = in ? (A)cf->C[j * MAXK + i] : A(0);
     }
     for (int e = threadIdx.x; e < KM; e += blockDim.x) {
         sS[e] = e < k ? (A)cf->scale[e] : A(0);
@@ -188,9 +259,9 @@ k_update(int64_t n, Tm *__restrict__ V, int ldv, const Ty *__restrict__ Y, int l
         sres[e] = 0.0;
     }
     __syncthreads();
-    A dv[KM], rs[KM];
+    A dv[STATS ? KM : 1], rs[STATS ? KM : 1];
 #pragma unroll
-    for (int i = 0; i < KM; ++i) {
+    for (int i = 0; i < (STATS ? KM : 1); ++i) {
         dv[i] = A(0);
         rs[i] = A(0);
     }
@@ -199,22 +270,21 @@ k_update(int64_t n, Tm *__restrict__ V, int ldv, const Ty *__restrict__ Y, int l
         Tm *vr = V + r * ldv;
         const Ty *yr = Y + r * ldy;
         A v[KM], y[KM];
-#pragma unroll
-        for (int j = 0; j < KM; ++j) {
-            v[j] = j < k ? cvt<A>(vr[j]) : A(0);
-            y[j] = j < k ? cvt<A>(__ldg(yr + j)) : A(0);
-        }
+        load_row<KM, false>(vr, k, vec != 0, v);
+        load_row<KM, true>(yr, k, vec != 0, y);
 #pragma unroll
         for (int i0 = 0; i0 < KM; i0 += 4) {
             if (i0 >= k) break;
             A s[4] = {A(0), A(0), A(0), A(0)}, pq[4] = {A(0), A(0), A(0), A(0)};
 #pragma unroll
             for (int j = 0; j < KM; ++j) {
-                const A *a4 = sA + j * KM + i0, *c4 = sC + j * KM + i0;
+                const A *a4 = sA + j * KM + i0;
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    s[q] += v[j] * a4[q];
-                    pq[q] += v[j] * c4[q];
+                for (int q = 0; q < 4; ++q) s[q] += v[j] * a4[q];
+                if (STATS) {
+                    const A *c4 = sC + j * KM + i0;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) pq[q] += v[j] * c4[q];
                 }
                 if (!bdiag) {
                     const A *b4 = sB + j * KM + i0;
@@ -222,22 +292,38 @@ k_update(int64_t n, Tm *__restrict__ V, int ldv, const Ty *__restrict__ Y, int l
                     for (int q = 0; q < 4; ++q) s[q] += y[j] * b4[q];
                 }
             }
+            alignas(16) Tm o[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int i = i0 + q;
                 if (bdiag) s[q] += y[i] * sB[i * KM + i];
                 s[q] *= sS[i];
-                const A d = s[q] - v[i];
-                dv[i] += d * d;
-                const A e = y[i] - pq[q];
-                rs[i] += e * e;
-                if (i < k) vr[i] = from_acc<Tm>(s[q]);
+                if (STATS) {
+                    const A d = s[q] - v[i];
+                    dv[STATS ? i : 0] += d * d;
+                    const A e = y[i] - pq[q];
+                    rs[STATS ? i : 0] += e * e;
+                }
+                o[q] = from_acc<Tm>(s[q]);
+            }
+            if (vec && i0 + 4 <= k) {
+                if (sizeof(Tm) == 4) {
+                    *reinterpret_cast<uint4 *>(vr + i0) = *reinterpret_cast<const uint4 *>(o);
+                } else {
+                    reinterpret_cast<uint4 *>(vr + i0)[0] = reinterpret_cast<const uint4 *>(o)[0];
+                    reinterpret_cast<uint4 *>(vr + i0)[1] = reinterpret_cast<const uint4 *>(o)[1];
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (i0 + q < k) vr[i0 + q] = o[q];
             }
         }
     }
+    if (!STATS) return;
     // column sums: warp shuffle, then shared, then one atomic per block and column
 #pragma unroll
-    for (int i = 0; i < KM; ++i) {
+    for (int i = 0; i < (STATS ? KM : 1); ++i) {
         A x = dv[i], z = rs[i];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -272,11 +358,21 @@ __global__ void k_rayleigh_out(const double *G, int k, double *out) {
 
 template <typename Tm, typename Ty>
 static sped_status run_update(int64_t n, void *V, int ldv, const void *Y, int ldy, int k,
-                              Coefs *cf, int bdiag, cudaStream_t st) {
+                              Coefs *cf, int bdiag, bool stats, cudaStream_t st) {
     int blocks = device_sm_count() * 4;
     const int64_t need = (n + 255) / 256;
     if (need < blocks) blocks = (int)(need > 0 ? need : 1);
-#define UPD(KMV) k_update<Tm, Ty, KMV><<<blocks, 256, 0, st>>>(n, (Tm *)V, ldv, (const Ty *)Y, ldy, k, cf, bdiag)
+    const int vec = ((uintptr_t)V % 16 == 0) && ((uintptr_t)Y % 16 == 0) &&
+                    (ldv * (int)sizeof(Tm)) % 16 == 0 && (ldy * (int)sizeof(Ty)) % 16 == 0;
+#define UPD(KMV)                                                                               \
+    do {                                                                                       \
+        if (stats)                                                                             \
+            k_update<Tm, Ty, KMV, true><<<blocks, 256, 0, st>>>(n, (Tm *)V, ldv, (const Ty *)Y, \
+                                                                ldy, k, cf, bdiag, vec);       \
+        else                                                                                   \
+            k_update<Tm, Ty, KMV, false><<<blocks, 256, 0, st>>>(n, (Tm *)V, ldv, (const Ty *)Y, \
+                                                                 ldy, k, cf, bdiag, vec);      \
+    } while (0)
     if (k <= 8) UPD(8);
     else if (k <= 16) UPD(16);
     else if (k <= 20) UPD(20);
@@ -348,10 +444,10 @@ static sped_status eig_step_impl(const sped_graph *g, const sped_step_opts *o, v
     k_small<<<1, SMALL_THREADS, 0, st>>>(G, k, o->eta, (int)o->solver, cf, d_stats);
     SPED_CHECK_LAUNCH("k_small");
     const int bdiag = o->solver == SPED_SOLVER_MU_EG;  // mu-EG: Y enters through eta I
-    if (vt == SPED_F32 && o->y_t == SPED_F32) SPED_TRY((run_update<float, float>(g->n, V, ld, Y, L.ldy, k, cf, bdiag, st)));
-    else if (vt == SPED_F32 && o->y_t == SPED_F64) SPED_TRY((run_update<float, double>(g->n, V, ld, Y, L.ldy, k, cf, bdiag, st)));
-    else if (vt == SPED_F64 && o->y_t == SPED_F64) SPED_TRY((run_update<double, double>(g->n, V, ld, Y, L.ldy, k, cf, bdiag, st)));
-    else if (vt == SPED_F64 && o->y_t == SPED_F32) SPED_TRY((run_update<double, float>(g->n, V, ld, Y, L.ldy, k, cf, bdiag, st)));
+    if (vt == SPED_F32 && o->y_t == SPED_F32) SPED_TRY((run_update<float, float>(g->n, V, ld, Y, L.ldy, k, cf, bdiag, d_stats != nullptr, st)));
+    else if (vt == SPED_F32 && o->y_t == SPED_F64) SPED_TRY((run_update<float, double>(g->n, V, ld, Y, L.ldy, k, cf, bdiag, d_stats != nullptr, st)));
+    else if (vt == SPED_F64 && o->y_t == SPED_F64) SPED_TRY((run_update<double, double>(g->n, V, ld, Y, L.ldy, k, cf, bdiag, d_stats != nullptr, st)));
+    else if (vt == SPED_F64 && o->y_t == SPED_F32) SPED_TRY((run_update<double, float>(g->n, V, ld, Y, L.ldy, k, cf, bdiag, d_stats != nullptr, st)));
     else return fail(SPED_ERR_UNSUPPORTED, "eig_step: master V must be F32 or F64");
     if (d_stats) {
         k_finish_stats<<<1, MAXK, 0, st>>>(k, cf, d_stats);
@@ -469,11 +565,15 @@ sped_status sped_solve_bottom_k(const sped_graph *g, const sped_solve_opts *opts
     double res = INFINITY;
     for (int step = 1; step <= opts->max_steps; ++step) {
         sped_step_opts so = phase_opts(opts, phase);
-        SPED_TRY(sped_eig_step(g, &so, d_V, v_t, k, ld, d_stats, d_scratch, body, stream));
+        // the statistics (Rayleigh quotients, residuals, step norms) cost a Cholesky solve and a
+        // second k x k product per row, so they are formed on check steps only
+        const bool check = step % opts->check_every == 0 || step == opts->max_steps;
+        SPED_TRY(sped_eig_step(g, &so, d_V, v_t, k, ld, check ? d_stats : nullptr, d_scratch,
+                               body, stream));
         rep.steps = step;
         rep.spmm_count += poly_spmm_count(g, so.mode);
         if (phase == 1) rep.phase1_steps = step;
-        if (step % opts->check_every == 0 || step == opts->max_steps) {
+        if (check) {
             SPED_CUDA(cudaMemcpyAsync(h_stats, d_stats, sizeof(double) * 3 * k,
                                       cudaMemcpyDeviceToHost, st));
             int h_err = 0;
