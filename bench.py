@@ -302,6 +302,164 @@ def cpu_baseline(g, sample_steps=None):
 
 
 # ----------------------------------------------------------------------------------------
+def _timed(torch, stream, fn, reps):
+    """Mean device time (ms) of fn() over reps calls, CUDA events on the launching stream."""
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def measure_stochastic(sped, torch, g, G, dev, stream, k, ell, reps=5, err_degrees=(1, 3, 7)):
+    """Sampled-term estimate of p(L)V (Section 4.3) on the benchmark graph with M = nnz
+    walkers, so that M l matches the nnz l row touches of the exact chain: walk steps per
+    second and effective GB/s (the exact F32 chain's algorithmic bytes over the estimate's time)
+    at the benchmark degree, and the relative error of one estimate against the exact F32 chain
+    at that and smaller degrees (the estimator samples the monomial expansion, whose terms grow
+    like (1 + s lambda)^l against a result of size |1 - s lambda|^l, so its variance explodes
+    with the degree)."""
+    M = g.nnz
+    V = sped.alloc_block(g.n, k, torch.float32, dev)
+    V[:, :k] = torch.from_numpy(gen.gaussian_block(g.n, k, seed=SEED + 11)).to(dev)
+    Yx = sped.alloc_block(g.n, k, torch.float32, dev)
+    Y = sped.alloc_block(g.n, k, torch.float32, dev)
+    scr = torch.empty(sped.apply_poly_scratch_bytes(G, k, torch.float32), dtype=torch.uint8,
+                      device=dev)
+    out = {"walkers": M, "degree": ell, "k": k}
+    seed = [SEED]
+    for deg in sorted(set(err_degrees) | {ell}):
+        G.set_polynomial(sped.POLY_LIMIT_EXP, deg)
+        exact = lambda: sped.apply_poly(G, V, Yx, k, chain_dtype=torch.float32, scratch=scr)
+        exact()
+        ynorm = float(torch.linalg.vector_norm(Yx[:, :k].double()))
+        rec = {}
+        if deg == ell:
+            rec["exact_f32_chain_ms"] = _timed(torch, stream, exact, reps)
+            rec["exact_f32_chain_bytes"] = deg * spmm_bytes(g.n, g.nnz, k, 4, 4)
+        for mode, name in ((sped.STOCHASTIC_IS, "importance_weighted"),
+                           (sped.STOCHASTIC_REJECT, "rejection")):
+            scr_s = torch.empty(sped.apply_poly_scratch_bytes(G, k, torch.float32, mode),
+                                dtype=torch.uint8, device=dev)
+
+            def est():
+                seed[0] += 1
+                sped.apply_poly(G, V, Y, k, chain_dtype=torch.float32, mode=mode, walkers=M,
+                                seed=seed[0], scratch=scr_s)
+            est()
+            torch.cuda.synchronize()
+            err = float(torch.linalg.vector_norm((Y[:, :k] - Yx[:, :k]).double())) / ynorm
+            r = {"relative_error_vs_exact": err}
+            if deg == ell:
+                ms = _timed(torch, stream, est, reps)
+                r.update({"ms": ms, "walk_steps_per_s": M * deg / (ms * 1e-3),
+                          "effective_gbs": rec["exact_f32_chain_bytes"] / (ms * 1e-3) / 1e9})
+            rec[name] = r
+            del scr_s
+        out[f"degree_{deg}"] = rec
+    G.set_polynomial(sped.POLY_LIMIT_EXP, ell)
+    return out
+
+
+def measure_batched(sped, torch, dev, stream, k=8, degree=31, steps=4):
+    """Many independent graphs in one persistent launch (Section 5 applied per graph): 4,096
+    SBMs with log-uniform sizes in [200, 20,000], 2-8 blocks, mean degree 12, 87.5 % of edge
+    ends inside blocks; k = 8, limit form of degree 31, BF16 chain, mu-EG."""
+    gs = gen.batched_sbm(4096)
+    B = sped.Batch.from_graphs(gs, degree=degree, device=dev)
+    n, nnz = B.n_total, int(B.col_idx.numel())
+    V = sped.batch_block(n, k, device=dev)
+    V[:, :k] = torch.from_numpy(gen.gaussian_block(n, k, seed=SEED + 13)).to(dev)
+    scr = torch.empty(B.scratch_bytes(k), dtype=torch.uint8, device=dev)
+    ritz = torch.empty((B.n_graphs, k), dtype=torch.float64, device=dev)
+    run = lambda: B.eig_steps(V, k, steps=steps, eta=1.0, ritz=ritz, scratch=scr)
+    run()
+    ms = _timed(torch, stream, run, 3) / steps
+    step_b = degree * spmm_bytes(n, nnz, k, 2, 2) + n * k * 4 * 2 + n * k * 4 * 3
+    peak, kind = _peaks()
+    return {"workload": f"batched_sbm_{B.n_graphs}graphs_n{n}_k{k}", "graphs": B.n_graphs,
+            "n_total": n, "nnz_total": nnz, "k": k, "degree_l": degree,
+            "ms_per_step": ms, "graph_steps_per_s": B.n_graphs / (ms * 1e-3),
+            "step_bytes": step_b, "gbs": step_b / (ms * 1e-3) / 1e9,
+            "frac_of_hbm": step_b / (ms * 1e-3) / 1e9 / peak, "peak_kind": kind,
+            "launches_per_call": 1, "steps_per_call": steps}
+
+
+def measure_differentiable(sped, torch, dev, stream, k=10, ell=11, reps=5):
+    """Forward (EigenGame utilities of the columns of V under (I - sL(w))^l) and backward
+    (adjoint chain for dV, checkpointed SDDMM for dw) on an SBM with N = 200,000, 10 blocks,
+    mean degree 20, 87.5 % intra-block edge ends, learnable weights U(0.5, 1.5), k = 10."""
+    g = gen.uniform_edge_weights(gen.sbm_by_degree(200_000, 10, 20.0, 0.875, seed=5), seed=6)
+    G = sped.Graph.from_csr(g, device=dev)
+    G.set_polynomial(sped.POLY_LIMIT_EXP, ell)
+    ne = G.info().n_edges
+    w = torch.from_numpy(np.random.default_rng(SEED + 17).uniform(0.5, 1.5, ne)).to(dev)
+    w = w.float().requires_grad_(True)
+    V = sped.alloc_block(g.n, k, torch.float32, dev)
+    V[:, :k] = torch.from_numpy(gen.gaussian_block(g.n, k, seed=SEED + 19)).to(dev)
+    V.requires_grad_(True)
+    gu = torch.linspace(1.0, 0.1, k, dtype=torch.float64, device=dev)
+
+    def fwd_bwd():
+        V.grad, w.grad = None, None
+        u = sped.eigengame_utilities(V, w, G, k)
+        (u * gu).sum().backward()
+    fwd_bwd()
+    ms = _timed(torch, stream, fwd_bwd, reps)
+    fwd = lambda: sped.eigengame_utilities(V.detach(), w.detach(), G, k)
+    fwd()
+    ms_f = _timed(torch, stream, fwd, reps)
+    return {"workload": f"sbm_n{g.n}_b10_deg20_k{k}_weighted", "n": g.n, "nnz": g.nnz,
+            "edges": ne, "k": k, "degree_l": ell, "dtype": "f32",
+            "forward_ms": ms_f, "forward_backward_ms": ms,
+            "backward_over_forward": (ms - ms_f) / ms_f}
+
+
+def measure_power_law(sped, torch, dev, stream, n=16_000_000, k=32, ell=251, target_nnz=None):
+    """Skewed-degree workload for the merge-path chain step: planted-cluster Chung-Lu graph
+    (power law gamma = 2.5 on expected degrees [4, 10^4], 64 clusters of log-normal sizes, 90 %
+    intra-cluster edge ends, weights U(0.5, 1.5)), k = 32, BF16 chain, limit form of degree
+    251 with s = 2 / lambda_bound. Times one merge-path step, one row-group step on the same
+    graph, and the whole p(L) V."""
+    t0 = time.perf_counter()
+    g = gen.chung_lu_clusters(n, target_nnz=target_nnz, seed=SEED)
+    gen_s = time.perf_counter() - t0
+    G = sped.Graph.from_csr(g, device=dev)
+    info = G.set_polynomial(sped.POLY_LIMIT_EXP, ell)
+    X = sped.alloc_block(g.n, k, torch.bfloat16, dev)
+    X[:, :k] = torch.randn(g.n, k, generator=torch.Generator(device=dev).manual_seed(SEED),
+                           device=dev).to(torch.bfloat16)
+    Y = sped.alloc_block(g.n, k, torch.bfloat16, dev)
+    one_b = spmm_bytes(g.n, g.nnz, k, 2, 2, weighted=True) + 4 * g.n
+    out = {"workload": f"chung_lu_n{g.n}_nnz{g.nnz}_k{k}_weighted", "n": g.n, "nnz": g.nnz,
+           "max_degree": int(np.max(np.diff(g.row_ptr))), "k": k, "degree_l": ell,
+           "scale_s": info.scale_s, "host_generation_s": gen_s, "bytes_per_step": one_b}
+    peak, kind = _peaks()
+    for split, name in ((2, "merge_path"), (1, "row_group")):
+        step = lambda: sped.poly_step(G, X, Y, k, alpha=0.0, beta=-info.scale_s, gamma=1.0,
+                                      split=split)
+        step()
+        ms = _timed(torch, stream, step, 5)
+        out[name] = {"step_ms": ms, "gbs": one_b / (ms * 1e-3) / 1e9,
+                     "frac_of_hbm": one_b / (ms * 1e-3) / 1e9 / peak}
+    V = sped.alloc_block(g.n, k, torch.float32, dev)
+    V[:, :k] = X[:, :k].float()
+    Yf = sped.alloc_block(g.n, k, torch.float32, dev)
+    scr = torch.empty(sped.apply_poly_scratch_bytes(G, k, torch.bfloat16), dtype=torch.uint8,
+                      device=dev)
+    full = lambda: sped.apply_poly(G, V, Yf, k, chain_dtype=torch.bfloat16, scratch=scr)
+    full()
+    ms = _timed(torch, stream, full, 1)
+    out["p_of_L_V_ms"] = ms
+    out["p_of_L_V_gbs"] = ell * one_b / (ms * 1e-3) / 1e9
+    out["peak_kind"] = kind
+    return out
+
+
+# ----------------------------------------------------------------------------------------
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -411,19 +569,28 @@ def run_ours(args, rank, world, local_rank):
            "h2d_bytes_per_step": vb, "d2h_bytes_per_step": vb, "ms_per_step": e2e_ms}
 
     extra = {}
+    if rank == 0 and not args.no_extra:
+        # gathered bytes of one chain step (every stored entry pulls one k-column row)
+        extra["gather_bytes_per_launch"] = g.nnz * k * 2
+        extra["stochastic"] = measure_stochastic(sped, torch, g, G, dev, stream, k, ell)
+        extra["differentiable"] = measure_differentiable(sped, torch, dev, stream)
+        extra["batched"] = measure_batched(sped, torch, dev, stream)
+    if rank == 0 and args.power_law:
+        extra["power_law"] = measure_power_law(sped, torch, dev, stream,
+                                               target_nnz=args.target_nnz)
     if rank == 0 and not args.no_ttk:
         # bottom-20 of this workload is not a well-conditioned subspace (Poisson low-degree
         # nodes put localized modes inside the block-mode cluster; `--spectrum` shows it), so
-        # time-to-bottom-k is measured on config 1 and on the near-regular SBM of the same size,
-        # block structure and mean degree
+        # time-to-bottom-k is measured on the small SBM (N = 2,000, 4 blocks, k = 4) and on the
+        # near-regular SBM of the benchmark's size, block structure and mean degree
         del scr
         g1 = gen.sbm(2000, 4, 0.05, 0.001, seed=SEED)
-        g1.name = "sbm_n2000_b4_config1"
+        g1.name = "sbm_n2000_b4_k4"
         g2 = gen.sbm_regular(w["n"], w["blocks"], 14, 2, seed=SEED)
         g2.name = f"sbm_regular_n{w['n']}_b{w['blocks']}_deg14+2"
         extra["time_to_bottom_k"] = {
-            "config1": time_to_bottom_k(sped, torch, g1, 4, dev, stream, 45),
-            "regular_sbm_1e6": time_to_bottom_k(sped, torch, g2, k, dev, stream, 41)}
+            "sbm_n2000_b4_k4": time_to_bottom_k(sped, torch, g1, 4, dev, stream, 45),
+            "sbm_regular_n1e6_b20_k20": time_to_bottom_k(sped, torch, g2, k, dev, stream, 41)}
     clocks = clk.summary()
     if rank != 0:
         return
@@ -452,6 +619,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-ttk", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the stochastic, differentiable and batched measurements")
+    ap.add_argument("--power-law", action="store_true",
+                    help="also time the merge-path chain on the 16M-node Chung-Lu graph "
+                         "(about 2 minutes of host-side graph generation)")
+    ap.add_argument("--target-nnz", type=float, default=None,
+                    help="scale the Chung-Lu expected degrees to this many stored entries")
     ap.add_argument("--spectrum", action="store_true",
                     help="print the bottom of the workload's spectrum and exit")
     args = ap.parse_args()

@@ -207,7 +207,7 @@ class Graph:
 
     @classmethod
     def from_csr(cls, g, device="cuda", check=True):
-        """From a gen.CSRGraph (numpy arrays)."""
+        """From a host CSR graph (an object with n, row_ptr, col_idx and optional w arrays)."""
         rp = torch.from_numpy(g.row_ptr).to(device)
         ci = torch.from_numpy(g.col_idx).to(device)
         w = None if g.w is None else torch.from_numpy(g.w).to(device)
@@ -414,12 +414,30 @@ class Batch:
 
     @classmethod
     def from_graphs(cls, graphs, degree=31, device="cuda", check=True):
-        import gen as _gen  # input generators only (no method arithmetic)
-        big, node_off, _ = _gen.concat_graphs(graphs)
-        rp = torch.from_numpy(big.row_ptr).to(device)
-        ci = torch.from_numpy(big.col_idx).to(device)
-        w = None if big.w is None else torch.from_numpy(big.w).to(device)
-        return cls(node_off, rp, ci, w, degree=degree, check=check)
+        """Block-diagonal union of host CSR graphs (objects with n, row_ptr, col_idx and an
+        optional w, all or none weighted), column ids shifted to global node ids."""
+        import numpy as np
+        n = np.array([g.n for g in graphs], dtype=np.int64)
+        nnz = np.array([len(g.col_idx) for g in graphs], dtype=np.int64)
+        node_off = np.concatenate([[0], np.cumsum(n)])
+        nnz_off = np.concatenate([[0], np.cumsum(nnz)])
+        if nnz_off[-1] > np.iinfo(np.int32).max or node_off[-1] > np.iinfo(np.int32).max:
+            raise ValueError("batch exceeds int32 indexing")
+        rp = np.empty(node_off[-1] + 1, dtype=np.int32)
+        ci = np.empty(nnz_off[-1], dtype=np.int32)
+        weighted = graphs[0].w is not None
+        if any((g.w is not None) != weighted for g in graphs):
+            raise ValueError("batch mixes weighted and unweighted graphs")
+        wv = np.empty(nnz_off[-1], dtype=np.float32) if weighted else None
+        rp[0] = 0
+        for i, g in enumerate(graphs):
+            rp[node_off[i] + 1: node_off[i + 1] + 1] = np.asarray(g.row_ptr[1:], np.int64) + nnz_off[i]
+            ci[nnz_off[i]: nnz_off[i + 1]] = np.asarray(g.col_idx, np.int64) + node_off[i]
+            if weighted:
+                wv[nnz_off[i]: nnz_off[i + 1]] = g.w
+        w = None if wv is None else torch.from_numpy(wv).to(device)
+        return cls(node_off, torch.from_numpy(rp).to(device), torch.from_numpy(ci).to(device),
+                   w, degree=degree, check=check)
 
     def __del__(self):
         h = getattr(self, "handle", None)

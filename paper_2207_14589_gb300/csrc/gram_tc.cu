@@ -26,8 +26,9 @@
 
 namespace sped {
 
-constexpr int TC_THREADS = 256;
-constexpr int TC_MAXQ = 8;           // 16-byte chunks per thread per tile
+constexpr int TC_THREADS = 512;
+constexpr int TC_MAXQ = 4;           // 16-byte chunks per thread per tile
+constexpr int TC_WARPS = TC_THREADS / 32;
 constexpr int TC_TILE = 128;          // graph rows per tile
 constexpr int TC_SLICES = TC_TILE / 16;
 constexpr int TC_SLICE_BYTES = 128 * 16 * 2;
@@ -38,6 +39,7 @@ constexpr uint32_t TC_WAIT_LIMIT = 1u << 22;
 
 struct TcSmem {
     alignas(1024) unsigned char stage[2][TC_STAGE_BYTES];
+    alignas(16) unsigned char raw[TC_MAXQ * TC_THREADS * 16];  // one tile of A and B as read
     float acc_hi[128 * 128];  // [n][m]
     float acc_lo[128 * 128];
     alignas(8) uint64_t mbar[2];
@@ -127,6 +129,8 @@ k_gram_tc(int64_t n, const Ta *__restrict__ A, int lda, int ka, const Tb *__rest
     const int t = threadIdx.x;
     const int warp = t >> 5;
     const int K2 = ka + kb;
+    const int c_first = t % K2, g_first = t / K2;                 // this thread's first split unit
+    const int c_step = TC_THREADS % K2, g_step = TC_THREADS / K2;  // and the stride between units
     // ---- set-up: zero operands and sums, barriers, tensor memory
     for (int e = t; e < 2 * TC_STAGE_BYTES / 16; e += TC_THREADS)
         reinterpret_cast<uint4 *>(&sm.stage[0][0])[e] = make_uint4(0, 0, 0, 0);
@@ -156,9 +160,9 @@ k_gram_tc(int64_t n, const Ta *__restrict__ A, int lda, int ka, const Tb *__rest
     bool fresh = true;  // next MMA overwrites the accumulator
     bool ok = true;
     const int64_t ntiles = (n + TC_TILE - 1) / TC_TILE;
-    // the 16-byte chunks of one tile held by this thread (loaded one tile ahead)
-    uint4 buf[TC_MAXQ];
-    auto load_tile = [&](int64_t tl) {
+    // the 16-byte chunks of the next two tiles held by this thread (two tiles in flight)
+    uint4 buf[TC_MAXQ], buf2[TC_MAXQ];
+    auto load_tile = [&](int64_t tl, uint4 (&dst)[TC_MAXQ]) {
         if (tl >= ntiles) return;
         const int64_t q0 = tl * TC_TILE;
         const int rws = (int)(n - q0 < TC_TILE ? n - q0 : TC_TILE);
@@ -166,11 +170,12 @@ k_gram_tc(int64_t n, const Ta *__restrict__ A, int lda, int ka, const Tb *__rest
 #pragma unroll
         for (int u = 0; u < TC_MAXQ; ++u) {
             const int q = t + u * TC_THREADS;
-            if (q < na) buf[u] = __ldg(reinterpret_cast<const uint4 *>(A + q0 * lda) + q);
-            else if (q - na < nb) buf[u] = __ldg(reinterpret_cast<const uint4 *>(B + q0 * ldb) + (q - na));
+            if (q < na) dst[u] = __ldg(reinterpret_cast<const uint4 *>(A + q0 * lda) + q);
+            else if (q - na < nb) dst[u] = __ldg(reinterpret_cast<const uint4 *>(B + q0 * ldb) + (q - na));
         }
     };
-    load_tile(blockIdx.x);
+    load_tile(blockIdx.x, buf);
+    load_tile(blockIdx.x + gridDim.x, buf2);
     int it = 0;
     for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it) {
         const int st = it & 1;
@@ -180,49 +185,60 @@ k_gram_tc(int64_t n, const Ta *__restrict__ A, int lda, int ka, const Tb *__rest
             pending[st] = false;
             if (!ok) break;
         }
-        // ---- stage: the tile's rows of A and B are contiguous (row stride lda / ldb), so the
-        // CTA reads them as 16-byte chunks in address order (all loads issued first), then each
-        // element is split into S BF16 pieces written into the K-major core-matrix layout
+        // ---- stage: the tile's rows of A and B are contiguous (row stride lda / ldb); the CTA
+        // read them as 16-byte chunks in address order two tiles ahead and now parks them in
+        // shared memory as they are
         const int64_t r0 = tile * TC_TILE;
         const int rows = (int)(n - r0 < TC_TILE ? n - r0 : TC_TILE);
         const int qa = rows * lda / EA, qb = rows * ldb / EB;  // chunks of A and of B
 #pragma unroll
         for (int u = 0; u < TC_MAXQ; ++u) {
             const int q = t + u * TC_THREADS;
-            const bool in_a = q < qa;
-            if (!in_a && q - qa >= qb) continue;
-            const int e0 = in_a ? q * EA : (q - qa) * EB;
-            const int ld = in_a ? lda : ldb;
-            const int row = e0 / ld, col0 = e0 - row * ld;
-            unsigned char *base = sm.stage[st] + (row >> 4) * TC_SLICE_BYTES;
-            const int kk = row & 15;
-            const int kofs = (kk >> 3) * 128 + (kk & 7) * 2;
-            const int ne = in_a ? EA : EB;
-            for (int e = 0; e < ne; ++e) {
-                const int col = col0 + e;
-                if (col >= (in_a ? ka : kb)) break;
-                float x = in_a ? cvt<float>(reinterpret_cast<const Ta *>(&buf[u])[e])
-                               : cvt<float>(reinterpret_cast<const Tb *>(&buf[u])[e]);
-                const int c = in_a ? col : ka + col;
+            if (q < qa + qb) reinterpret_cast<uint4 *>(sm.raw)[q] = buf[u];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < TC_MAXQ; ++u) buf[u] = buf2[u];
+        load_tile(tile + 2 * (int64_t)gridDim.x, buf2);  // flies during two splits and MMAs
+        // ---- split: unit (c, g) is column c of [A B] over graph rows 8g .. 8g+7 (zero past the
+        // end); each of its S BF16 pieces is 8 consecutive K elements, i.e. one 16-byte row of
+        // a core matrix (operand row m = s K2 + c, K half g & 1 of slice g / 2)
+        {
+            const Ta *ra = reinterpret_cast<const Ta *>(sm.raw);
+            const Tb *rb = reinterpret_cast<const Tb *>(sm.raw + (size_t)qa * 16);
+            // unit uu = g K2 + c, advanced by TC_THREADS without a division per unit
+            int c = c_first, g = g_first;
+            for (; g < TC_TILE / 8; c += c_step, g += g_step) {
+                if (c >= K2) {
+                    c -= K2;
+                    ++g;
+                    if (g >= TC_TILE / 8) break;
+                }
+                float x[8];
+#pragma unroll
+                for (int rr = 0; rr < 8; ++rr) {
+                    const int row = g * 8 + rr;
+                    x[rr] = row >= rows ? 0.f
+                            : c < ka    ? cvt<float>(ra[row * lda + c])
+                                        : cvt<float>(rb[row * ldb + (c - ka)]);
+                }
+                unsigned char *slice = sm.stage[st] + (g >> 1) * TC_SLICE_BYTES + (g & 1) * 128;
 #pragma unroll
                 for (int s = 0; s < S; ++s) {
-                    const __nv_bfloat16 h = __float2bfloat16_rn(x);
-                    x -= __bfloat162float(h);
+                    uint32_t w[4];
+#pragma unroll
+                    for (int p2 = 0; p2 < 4; ++p2) {
+                        const __nv_bfloat162 h2 = __floats2bfloat162_rn(x[2 * p2], x[2 * p2 + 1]);
+                        w[p2] = *reinterpret_cast<const uint32_t *>(&h2);
+                        if (s + 1 < S) {  // the rounding residual is exact in F32
+                            x[2 * p2] -= __low2float(h2);
+                            x[2 * p2 + 1] -= __high2float(h2);
+                        }
+                    }
                     const int m = s * K2 + c;
-                    *reinterpret_cast<__nv_bfloat16 *>(base + ((m >> 3) * 2) * 128 +
-                                                       (m & 7) * 16 + kofs) = h;
+                    *reinterpret_cast<uint4 *>(slice + (m >> 3) * 256 + (m & 7) * 16) =
+                        make_uint4(w[0], w[1], w[2], w[3]);
                 }
-            }
-        }
-        load_tile(tile + gridDim.x);  // next tile's chunks fly during the MMA and the fold
-        if (rows < TC_TILE) {  // tail tile: zero the rows past the end (all pieces)
-            for (int e = t; e < (TC_TILE - rows) * S * K2; e += TC_THREADS) {
-                const int row = rows + e / (S * K2), m = e % (S * K2);
-                const int kk = row & 15;
-                *reinterpret_cast<__nv_bfloat16 *>(sm.stage[st] + (row >> 4) * TC_SLICE_BYTES +
-                                                   ((m >> 3) * 2) * 128 + (m & 7) * 16 +
-                                                   (kk >> 3) * 128 + (kk & 7) * 2) =
-                    __float2bfloat16_rn(0.f);
             }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -247,10 +263,11 @@ k_gram_tc(int64_t n, const Ta *__restrict__ A, int lda, int ka, const Tb *__rest
             pending[st] = false;
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;");
-            // warp w reads lane quarter w % 4 (its own TMEM lanes), column half w / 4
+            // warp w reads lane quarter w % 4 (its own TMEM lanes), column slice w / 4
             const int lane_m = (warp & 3) * 32 + (t & 31);
+            constexpr int CW = TC_COLS / (TC_WARPS / 4);  // columns per warp
 #pragma unroll 1
-            for (int c0 = (warp >> 2) * (TC_COLS / 2); c0 < ((warp >> 2) + 1) * (TC_COLS / 2); c0 += 32) {
+            for (int c0 = (warp >> 2) * CW; c0 < ((warp >> 2) + 1) * CW; c0 += 32) {
                 uint32_t v[32];
                 const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)c0;
                 asm volatile(
@@ -312,13 +329,26 @@ k_gram_tc(int64_t n, const Ta *__restrict__ A, int lda, int ka, const Tb *__rest
     }
 }
 
-__global__ void k_gram_tc_reduce(const double *__restrict__ partial, int nparts, int K2,
-                                 double *__restrict__ G) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= K2 * K2) return;
+// G[e] = sum over CTAs of partial[c][e]: a block per 32 outputs, 8 thread groups over the
+// partials, then a fixed-order sum of the 8 group totals (deterministic)
+constexpr int RED_OUT = 32, RED_GROUPS = 8;
+__global__ void __launch_bounds__(RED_OUT *RED_GROUPS)
+k_gram_tc_reduce(const double *__restrict__ partial, int nparts, int K2, double *__restrict__ G) {
+    __shared__ double sm[RED_GROUPS][RED_OUT];
+    const int o = threadIdx.x % RED_OUT, grp = threadIdx.x / RED_OUT;
+    const int e = blockIdx.x * RED_OUT + o;
+    const int tot = K2 * K2;
     double s = 0.0;
-    for (int c = 0; c < nparts; ++c) s += partial[(int64_t)c * K2 * K2 + e];
-    G[e] = s;
+    if (e < tot)
+        for (int c = grp; c < nparts; c += RED_GROUPS) s += partial[(int64_t)c * tot + e];
+    sm[grp][o] = s;
+    __syncthreads();
+    if (grp == 0 && e < tot) {
+        double r = 0.0;
+#pragma unroll
+        for (int q = 0; q < RED_GROUPS; ++q) r += sm[q][o];
+        G[e] = r;
+    }
 }
 
 static int tc_ctas(int64_t n) {
@@ -356,7 +386,8 @@ static sped_status run_tc(int64_t n, const void *A, int lda, int ka, const void 
                                          partial);
     SPED_CHECK_LAUNCH("k_gram_tc");
     const int K2 = ka + kb;
-    k_gram_tc_reduce<<<(K2 * K2 + 255) / 256, 256, 0, st>>>(partial, ctas, K2, G);
+    k_gram_tc_reduce<<<(K2 * K2 + RED_OUT - 1) / RED_OUT, RED_OUT * RED_GROUPS, 0, st>>>(
+        partial, ctas, K2, G);
     SPED_CHECK_LAUNCH("k_gram_tc_reduce");
     return SPED_OK;
 }

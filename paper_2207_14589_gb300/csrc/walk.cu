@@ -32,16 +32,6 @@ struct WalkCoefs {
     double c[WALK_MAX_ELL + 1];
 };
 
-__device__ __forceinline__ double inc_dot(int a1, int b1, double w1, int a2, int b2, double w2) {
-    // both edges already ordered (a < b); signs: +1 at the smaller node, -1 at the larger
-    double d = 0.0;
-    if (a1 == a2) d += 1.0;
-    if (a1 == b2) d -= 1.0;
-    if (b1 == a2) d -= 1.0;
-    if (b1 == b2) d += 1.0;
-    return sqrt(w1) * sqrt(w2) * d;
-}
-
 template <typename Ty, typename Tv>
 __global__ void k_walk_init(int64_t n, int k, const Tv *__restrict__ V, int ldv, double c0,
                             Ty *__restrict__ Y, int ldy) {
@@ -52,13 +42,37 @@ __global__ void k_walk_init(int64_t n, int k, const Tv *__restrict__ V, int ldv,
     Y[r * ldy + j] = from_acc<Ty>(c0 * cvt<double>(V[r * ldv + j]));
 }
 
-template <typename Tv, typename Ty, bool W, int KM>
+// One row of V into registers (the k used columns; 16-byte loads when the layout allows it).
+template <int KM, typename Tv, typename A>
+__device__ __forceinline__ void walk_row(const Tv *p, int k, bool vec, A *out) {
+    constexpr int E = 16 / (int)sizeof(Tv);
+    if (vec && KM % E == 0) {
+#pragma unroll
+        for (int q = 0; q < KM / E; ++q) {
+            uint4 c = make_uint4(0, 0, 0, 0);
+            if (q * E < k) c = __ldg(reinterpret_cast<const uint4 *>(p) + q);
+            const Tv *e = reinterpret_cast<const Tv *>(&c);
+#pragma unroll
+            for (int u = 0; u < E; ++u) out[q * E + u] = cvt<A>(e[u]);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < KM; ++j) out[j] = j < k ? cvt<A>(__ldg(p + j)) : A(0);
+    }
+}
+
+// The walk's bookkeeping (edge draws, alpha, 1/q, the acceptance product) runs in FP64 and in
+// the oracle's order, so every sampled decision is the same; the k-column accumulation of
+// scale_i (V[a_i] - V[b_i]) runs in the output's precision (F32 output: F32 products of the
+// F32 difference with the FP64 scale rounded once per term).
+template <typename Tv, typename Ty, bool W, int KM, int MODE>
 __global__ void __launch_bounds__(WALK_THREADS)
 k_walk(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const float *__restrict__ w,
        const int32_t *__restrict__ rev, const int32_t *__restrict__ edge_p,
        const int32_t *__restrict__ edge_a, int64_t n_edges, const Tv *__restrict__ V, int ldv,
-       int k, int ell, int64_t walkers, uint64_t seed, int mode, double dstar_inc, WalkCoefs cf,
+       int k, int ell, int64_t walkers, uint64_t seed, double dstar_inc, int vec, WalkCoefs cf,
        Ty *__restrict__ Y, int ldy) {
+    using A = typename AccOf<Ty>::type;
     const double inv_m = 1.0 / (double)walkers;
     for (int64_t wk = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; wk < walkers;
          wk += (int64_t)gridDim.x * blockDim.x) {
@@ -67,28 +81,30 @@ k_walk(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const flo
         const int e1 = (int)s0.bounded((uint32_t)n_edges);
         int pc = __ldg(edge_p + e1);
         const int a1 = __ldg(edge_a + e1), b1 = __ldg(ci + pc);
-        const double w1 = W ? (double)__ldg(w + pc) : 1.0;
+        const double sw1 = W ? sqrt((double)__ldg(w + pc)) : 1.0;
         int a = a1, b = b1;
-        double wc = w1;
-        double alpha = 1.0, inv_q = (double)n_edges, accept = 1.0;
-        double acc[KM];
+        double swc = sw1;
+        double alpha = 1.0, inv_q = (double)n_edges, accept = 1.0, inv_pmin = (double)n_edges;
+        A acc[KM];
 #pragma unroll
-        for (int j = 0; j < KM; ++j) acc[j] = 0.0;
+        for (int j = 0; j < KM; ++j) acc[j] = A(0);
         for (int i = 1; i <= ell; ++i) {
             double scale;
-            if (mode == SPED_STOCHASTIC_IS) {
-                scale = cf.c[i] * alpha * inv_q * sqrt(w1) * sqrt(wc);
+            if (MODE == SPED_STOCHASTIC_IS) {
+                scale = cf.c[i] * alpha * inv_q * sw1 * swc;
             } else {
                 WordStream su(seed, wlo, whi, 0x80000000u | (uint32_t)i);
-                double u = ((double)su.next() + 0.5) * (1.0 / 4294967296.0);
-                double inv_pmin = (double)n_edges * pow(dstar_inc, (double)(i - 1));
-                scale = (u < accept) ? cf.c[i] * alpha * inv_pmin * sqrt(w1) * sqrt(wc) : 0.0;
+                const double u = ((double)su.next() + 0.5) * (1.0 / 4294967296.0);
+                scale = (u < accept) ? cf.c[i] * alpha * inv_pmin * sw1 * swc : 0.0;
+                inv_pmin *= dstar_inc;
             }
             if (scale != 0.0) {
-                const Tv *va = V + (int64_t)a * ldv, *vb = V + (int64_t)b * ldv;
+                A va[KM], vb[KM];
+                walk_row<KM>(V + (int64_t)a * ldv, k, vec != 0, va);
+                walk_row<KM>(V + (int64_t)b * ldv, k, vec != 0, vb);
+                const A sc = (A)scale;
 #pragma unroll
-                for (int j = 0; j < KM; ++j)
-                    if (j < k) acc[j] += scale * (cvt<double>(va[j]) - cvt<double>(vb[j]));
+                for (int j = 0; j < KM; ++j) acc[j] += sc * (va[j] - vb[j]);
             }
             if (i == ell) break;
             const int ra = __ldg(rp + a), da = __ldg(rp + a + 1) - ra;
@@ -109,21 +125,29 @@ k_walk(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const flo
             nb = __ldg(ci + q);
             const int lo = na < nb ? na : nb, hi = na < nb ? nb : na;
             const int pos = na < nb ? q : __ldg(rev + q);  // entry (lo, hi) in row lo
-            const double wn = W ? (double)__ldg(w + pos) : 1.0;
-            alpha *= inc_dot(a, b, wc, lo, hi, wn);
+            const double swn = W ? sqrt((double)__ldg(w + pos)) : 1.0;
+            // incidence inner product of {a, b} and {lo, hi} (+1 at the smaller node, -1 at the
+            // larger), times sqrt(w_e w_f)
+            double d = 0.0;
+            if (a == lo) d += 1.0;
+            if (a == hi) d -= 1.0;
+            if (b == lo) d -= 1.0;
+            if (b == hi) d += 1.0;
+            alpha *= swc * swn * d;
             inv_q *= (double)deg_inc;
-            accept *= (double)deg_inc / dstar_inc;
+            if (MODE != SPED_STOCHASTIC_IS) accept *= (double)deg_inc / dstar_inc;
             a = lo;
             b = hi;
             pc = pos;
-            wc = wn;
+            swc = swn;
         }
         Ty *ya = Y + (int64_t)a1 * ldy, *yb = Y + (int64_t)b1 * ldy;
+        const A im = (A)inv_m;
 #pragma unroll
         for (int j = 0; j < KM; ++j) {
-            if (j < k && acc[j] != 0.0) {
-                atomicAdd(ya + j, (Ty)(acc[j] * inv_m));
-                atomicAdd(yb + j, (Ty)(-acc[j] * inv_m));
+            if (j < k && acc[j] != A(0)) {
+                atomicAdd(ya + j, (Ty)(acc[j] * im));
+                atomicAdd(yb + j, (Ty)(-acc[j] * im));
             }
         }
     }
@@ -142,24 +166,31 @@ static sped_status run_walk(const sped_graph *g, int k, const void *V, int ldv, 
     WalkCoefs cf;
     for (int i = 0; i <= WALK_MAX_ELL; ++i) cf.c[i] = i <= ell ? P.power[i] : 0.0;
     double dstar_inc = 2.0 * g->max_deg - 1.0;
+    const int vec = ((uintptr_t)V % 16 == 0) && ((size_t)ldv * (sizeof(Tv)) % 16 == 0);
     int64_t blocks = (walkers + WALK_THREADS - 1) / WALK_THREADS;
     int64_t cap = (int64_t)device_sm_count() * 16;
     if (blocks > cap) blocks = cap;
+#define WALK3(KMV, WV, MV)                                                                     \
+    k_walk<Tv, Ty, WV, KMV, MV><<<(unsigned)blocks, WALK_THREADS, 0, st>>>(                    \
+        g->rp, g->ci, g->w, g->rev, g->edge_p, g->edge_a, g->n_edges, (const Tv *)V, ldv, k, ell, \
+        walkers, seed, dstar_inc, vec, cf, (Ty *)Y, ldy)
 #define WALK(KMV)                                                                              \
     do {                                                                                       \
-        if (g->w)                                                                              \
-            k_walk<Tv, Ty, true, KMV><<<(unsigned)blocks, WALK_THREADS, 0, st>>>(              \
-                g->rp, g->ci, g->w, g->rev, g->edge_p, g->edge_a, g->n_edges, (const Tv *)V,   \
-                ldv, k, ell, walkers, seed, (int)mode, dstar_inc, cf, (Ty *)Y, ldy);           \
-        else                                                                                   \
-            k_walk<Tv, Ty, false, KMV><<<(unsigned)blocks, WALK_THREADS, 0, st>>>(             \
-                g->rp, g->ci, g->w, g->rev, g->edge_p, g->edge_a, g->n_edges, (const Tv *)V,   \
-                ldv, k, ell, walkers, seed, (int)mode, dstar_inc, cf, (Ty *)Y, ldy);           \
+        if (g->w) {                                                                            \
+            if (mode == SPED_STOCHASTIC_IS) WALK3(KMV, true, SPED_STOCHASTIC_IS);              \
+            else WALK3(KMV, true, SPED_STOCHASTIC_REJECT);                                     \
+        } else {                                                                               \
+            if (mode == SPED_STOCHASTIC_IS) WALK3(KMV, false, SPED_STOCHASTIC_IS);             \
+            else WALK3(KMV, false, SPED_STOCHASTIC_REJECT);                                    \
+        }                                                                                      \
     } while (0)
     if (k <= 8) WALK(8);
     else if (k <= 16) WALK(16);
+    else if (k <= 20) WALK(20);
+    else if (k <= 24) WALK(24);
     else WALK(32);
 #undef WALK
+#undef WALK3
     SPED_CHECK_LAUNCH("k_walk");
     return SPED_OK;
 }

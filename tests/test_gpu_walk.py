@@ -39,6 +39,26 @@ def test_walk_same_draws_as_oracle(mode, gname, ell, k):
     assert rel(host(Y, k), want) <= 1e-11
 
 
+@pytest.mark.parametrize("mode", [sped.STOCHASTIC_IS, sped.STOCHASTIC_REJECT])
+@pytest.mark.parametrize("ell,k", [(3, 5), (7, 20), (5, 13)])
+def test_walk_fp32_same_draws_as_oracle(mode, ell, k):
+    # F32 blocks: the walk's draws and weights stay FP64 (same decisions as the oracle); the
+    # per-walker sums are F32, so agreement is to F32 rounding of each term
+    g = gen.uniform_edge_weights(gen.random_graph(250, 800, seed=5, hub=1, hub_degree=60), seed=6)
+    G = sped.Graph.from_csr(g)
+    G.set_polynomial(sped.POLY_LIMIT_EXP, ell, scale=0.01)
+    c = np.array(G.power_coeffs())
+    V0 = gen.gaussian_block(g.n, k, seed=8)
+    V = to_block(V0, torch.float32)
+    Y = sped.alloc_block(g.n, k, torch.float32, DEV)
+    walkers, seed = 20000, 987654321
+    sped.apply_poly(G, V, Y, k, mode=mode, walkers=walkers, seed=seed)
+    torch.cuda.synchronize()
+    want = oracle.walk_estimate(g, V0.astype(np.float32).astype(np.float64), c, walkers, seed,
+                                mode=mode)
+    assert rel(host(Y, k), want) <= 2e-5
+
+
 def test_walk_fp32_output_and_mean():
     g = gen.from_edges(6, [0, 1, 2, 3, 0, 1], [1, 2, 3, 4, 2, 5])
     G = sped.Graph.from_csr(g)
