@@ -48,47 +48,82 @@ __global__ void k_eg_util(int k, const double *__restrict__ H, int ldh,
     }
 }
 
-// Out = A P (+ B Q), P, Q k x k row-major FP64 (Out[r][i] = sum_j A[r][j] P[j][i] + ...)
-template <typename T>
-__global__ void k_combine(int64_t n, int k, const T *__restrict__ A, int lda,
-                          const double *__restrict__ P, const T *__restrict__ B, int ldb,
-                          const double *__restrict__ Q, T *__restrict__ Out, int ldo) {
-    __shared__ double sP[BW_MAXK * BW_MAXK], sQ[BW_MAXK * BW_MAXK];
-    for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
-        sP[e] = P[e];
-        sQ[e] = Q ? Q[e] : 0.0;
+// Out = A P (+ B Q), P, Q k x k row-major FP64 (Out[r][i] = sum_j A[r][j] P[j][i] + ...), one
+// row per thread, in the block's own precision (FP64 blocks: FP64; F32 blocks: F32 with the
+// coefficients rounded once), the row and the coefficients unrolled to KM >= k columns.
+template <typename T, int KM>
+__global__ void __launch_bounds__(256)
+k_combine(int64_t n, int k, const T *__restrict__ A, int lda, const double *__restrict__ P,
+          const T *__restrict__ B, int ldb, const double *__restrict__ Q, T *__restrict__ Out,
+          int ldo) {
+    using Acc = typename AccOf<T>::type;
+    __shared__ Acc sP[KM * KM], sQ[KM * KM];
+    for (int e = threadIdx.x; e < KM * KM; e += blockDim.x) {
+        const int j = e / KM, i = e % KM;
+        const bool in = i < k && j < k;
+        sP[e] = in ? (Acc)P[j * k + i] : Acc(0);
+        sQ[e] = in && Q ? (Acc)Q[j * k + i] : Acc(0);
     }
     __syncthreads();
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
-    double a[BW_MAXK], b[BW_MAXK];
-    for (int j = 0; j < k; ++j) {
-        a[j] = cvt<double>(A[r * lda + j]);
-        b[j] = B ? cvt<double>(B[r * ldb + j]) : 0.0;
+    Acc a[KM], b[KM];
+#pragma unroll
+    for (int j = 0; j < KM; ++j) {
+        a[j] = j < k ? cvt<Acc>(A[r * lda + j]) : Acc(0);
+        b[j] = (B && j < k) ? cvt<Acc>(B[r * ldb + j]) : Acc(0);
     }
-    for (int i = 0; i < k; ++i) {
-        double s = 0.0;
-        for (int j = 0; j < k; ++j) s += a[j] * sP[j * k + i] + b[j] * sQ[j * k + i];
+#pragma unroll
+    for (int i = 0; i < KM; ++i) {
+        if (i >= k) break;
+        Acc s = Acc(0);
+#pragma unroll
+        for (int j = 0; j < KM; ++j) s += a[j] * sP[j * KM + i] + b[j] * sQ[j * KM + i];
         Out[r * ldo + i] = from_acc<T>(s);
     }
 }
 
-// grad[e] += scale * (A[a] - A[b]) . (C[a] - C[b]) for every undirected edge e = (a, b)
-template <typename T>
-__global__ void k_sddmm(int64_t n_edges, const int32_t *__restrict__ edge_a,
-                        const int32_t *__restrict__ edge_p, const int32_t *__restrict__ ci, int k,
-                        const T *__restrict__ A, const T *__restrict__ C, int ld, double scale,
-                        double *__restrict__ grad) {
+// grad[e] += scale * (A[a] - A[b]) . (C[a] - C[b]) for every undirected edge e = (a, b); the
+// k-term dot in the blocks' precision, the accumulation into grad in FP64
+template <typename T, int KM>
+__global__ void __launch_bounds__(256)
+k_sddmm(int64_t n_edges, const int32_t *__restrict__ edge_a, const int32_t *__restrict__ edge_p,
+        const int32_t *__restrict__ ci, int k, const T *__restrict__ A, const T *__restrict__ C,
+        int ld, double scale, double *__restrict__ grad) {
+    using Acc = typename AccOf<T>::type;
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n_edges) return;
-    const int a = edge_a[e], b = ci[edge_p[e]];
-    double s = 0.0;
-    for (int i = 0; i < k; ++i) {
-        const double da = cvt<double>(A[(int64_t)a * ld + i]) - cvt<double>(A[(int64_t)b * ld + i]);
-        const double dc = cvt<double>(C[(int64_t)a * ld + i]) - cvt<double>(C[(int64_t)b * ld + i]);
-        s += da * dc;
+    const int a = __ldg(edge_a + e), b = __ldg(ci + __ldg(edge_p + e));
+    const T *Aa = A + (int64_t)a * ld, *Ab = A + (int64_t)b * ld;
+    const T *Ca = C + (int64_t)a * ld, *Cb = C + (int64_t)b * ld;
+    Acc s = Acc(0);
+#pragma unroll
+    for (int i = 0; i < KM; ++i) {
+        if (i < k) {
+            const Acc da = cvt<Acc>(__ldg(Aa + i)) - cvt<Acc>(__ldg(Ab + i));
+            const Acc dc = cvt<Acc>(__ldg(Ca + i)) - cvt<Acc>(__ldg(Cb + i));
+            s += da * dc;
+        }
     }
-    grad[e] += scale * s;
+    grad[e] += scale * (double)s;
+}
+
+template <typename T>
+static void launch_combine(int64_t n, int k, const T *A, int lda, const double *P, const T *B,
+                           int ldb, const double *Q, T *Out, int ldo, cudaStream_t st) {
+    const unsigned nb = (unsigned)((n + 255) / 256);
+    if (k <= 8) k_combine<T, 8><<<nb, 256, 0, st>>>(n, k, A, lda, P, B, ldb, Q, Out, ldo);
+    else if (k <= 16) k_combine<T, 16><<<nb, 256, 0, st>>>(n, k, A, lda, P, B, ldb, Q, Out, ldo);
+    else k_combine<T, 32><<<nb, 256, 0, st>>>(n, k, A, lda, P, B, ldb, Q, Out, ldo);
+}
+
+template <typename T>
+static void launch_sddmm(const sped_graph *g, int k, const T *A, const T *C, int ld, double scale,
+                         double *grad, cudaStream_t st) {
+    const unsigned eb = (unsigned)((g->n_edges + 255) / 256);
+    if (k <= 8) k_sddmm<T, 8><<<eb, 256, 0, st>>>(g->n_edges, g->edge_a, g->edge_p, g->ci, k, A, C, ld, scale, grad);
+    else if (k <= 16) k_sddmm<T, 16><<<eb, 256, 0, st>>>(g->n_edges, g->edge_a, g->edge_p, g->ci, k, A, C, ld, scale, grad);
+    else k_sddmm<T, 32><<<eb, 256, 0, st>>>(g->n_edges, g->edge_a, g->edge_p, g->ci, k, A, C, ld, scale, grad);
 }
 
 static int ckpt_stride(int ell) {
@@ -128,14 +163,13 @@ static sped_status run_edge_grad(const sped_graph *g, const T *V, int ldv, int k
     T *Aa = blk(L.nck + L.c), *Ab = blk(L.nck + L.c + 1);
     Scratch step_scr(base + L.block * (size_t)(L.nck + L.c + 2),
                      bytes - L.block * (size_t)(L.nck + L.c + 2));
-    const unsigned nb = (unsigned)((g->n + 255) / 256);
     auto step = [&](const T *X, T *Y) {
         step_scr.used = 0;
         return launch_poly_step(g, k, X, t, L.ld, nullptr, t, L.ld, Y, t, L.ld, 0.0, -s, 1.0, 0,
                                 step_scr, st);
     };
     // C_0 = V Hbar^T into checkpoint 0, then the forward C chain keeping every c-th block
-    k_combine<T><<<nb, 256, 0, st>>>(g->n, k, V, ldv, Hbar_T, nullptr, 0, nullptr, ck0, L.ld);
+    launch_combine<T>(g->n, k, V, ldv, Hbar_T, nullptr, 0, nullptr, ck0, L.ld, st);
     SPED_CHECK_LAUNCH("k_combine");
     for (int j = 1; j < L.nck; ++j) {
         const T *src = blk(j - 1);
@@ -152,7 +186,7 @@ static sped_status run_edge_grad(const sped_graph *g, const T *V, int ldv, int k
     double *d_eye = (double *)step_scr.take(sizeof(double) * k * k);
     if (!d_eye) return fail(SPED_ERR_SCRATCH, "edge_grad: scratch too small");
     SPED_CUDA(cudaMemcpyAsync(d_eye, eye.data(), sizeof(double) * k * k, cudaMemcpyHostToDevice, st));
-    k_combine<T><<<nb, 256, 0, st>>>(g->n, k, V, ldv, d_eye, nullptr, 0, nullptr, Aa, L.ld);
+    launch_combine<T>(g->n, k, V, ldv, d_eye, nullptr, 0, nullptr, Aa, L.ld, st);
     SPED_CHECK_LAUNCH("k_combine");
     const size_t keep = step_scr.used;
     auto step2 = [&](const T *X, T *Y) {
@@ -161,7 +195,6 @@ static sped_status run_edge_grad(const sped_graph *g, const T *V, int ldv, int k
                                 step_scr, st);
     };
     SPED_CUDA(cudaMemsetAsync(grad, 0, sizeof(double) * g->n_edges, st));
-    const unsigned eb = (unsigned)((g->n_edges + 255) / 256);
     int t_cur = 0;
     T *A = Aa, *Anext = Ab;
     for (int j = L.nck - 1; j >= 0; --j) {
@@ -172,9 +205,7 @@ static sped_status run_edge_grad(const sped_graph *g, const T *V, int ldv, int k
         for (int m = 1; m < len; ++m) SPED_TRY(step2(blk(L.nck + m - 1), blk(L.nck + m)));
         for (int m = len - 1; m >= 0; --m) {
             // u = j c + m pairs with t = l - 1 - u (t runs forward)
-            if (g->n_edges > 0)
-                k_sddmm<T><<<eb, 256, 0, st>>>(g->n_edges, g->edge_a, g->edge_p, g->ci, k, A,
-                                              blk(L.nck + m), L.ld, -s, grad);
+            if (g->n_edges > 0) launch_sddmm<T>(g, k, A, blk(L.nck + m), L.ld, -s, grad, st);
             SPED_CHECK_LAUNCH("k_sddmm");
             if (t_cur + 1 < ell) {
                 SPED_TRY(step2(A, Anext));
@@ -213,13 +244,12 @@ sped_status sped_block_combine(int64_t n, int k, const void *d_A, int lda, const
         return fail(SPED_ERR_INVALID_ARG, "block_combine: bad arguments");
     if (t != SPED_F32 && t != SPED_F64) return fail(SPED_ERR_UNSUPPORTED, "block_combine: F32/F64");
     if (n == 0) return SPED_OK;
-    const unsigned nb = (unsigned)((n + 255) / 256);
     if (t == SPED_F64)
-        k_combine<double><<<nb, 256, 0, as_stream(stream)>>>(
-            n, k, (const double *)d_A, lda, d_P, (const double *)d_B, ldb, d_Q, (double *)d_Out, ldo);
+        launch_combine<double>(n, k, (const double *)d_A, lda, d_P, (const double *)d_B, ldb, d_Q,
+                               (double *)d_Out, ldo, as_stream(stream));
     else
-        k_combine<float><<<nb, 256, 0, as_stream(stream)>>>(
-            n, k, (const float *)d_A, lda, d_P, (const float *)d_B, ldb, d_Q, (float *)d_Out, ldo);
+        launch_combine<float>(n, k, (const float *)d_A, lda, d_P, (const float *)d_B, ldb, d_Q,
+                              (float *)d_Out, ldo, as_stream(stream));
     SPED_CHECK_LAUNCH("k_combine");
     return SPED_OK;
 }
