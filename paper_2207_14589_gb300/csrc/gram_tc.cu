@@ -26,9 +26,10 @@
 
 namespace sped {
 
-constexpr int TC_THREADS = 512;
-constexpr int TC_MAXQ = 4;           // 16-byte chunks per thread per tile
-constexpr int TC_WARPS = TC_THREADS / 32;
+constexpr int TC_THREADS = 640;       // 20 warps: one split unit per thread at k = 20 (K2 = 40)
+constexpr int TC_RAW_CHUNKS = 2048;   // 16-byte chunks of one tile of A and B at most
+constexpr int TC_MAXQ = (TC_RAW_CHUNKS + TC_THREADS - 1) / TC_THREADS;  // per thread
+constexpr int TC_FOLD_WARPS = 16;     // warps that read the accumulator (4 per TMEM lane quarter)
 constexpr int TC_TILE = 128;          // graph rows per tile
 constexpr int TC_SLICES = TC_TILE / 16;
 constexpr int TC_SLICE_BYTES = 128 * 16 * 2;
@@ -39,7 +40,7 @@ constexpr uint32_t TC_WAIT_LIMIT = 1u << 22;
 
 struct TcSmem {
     alignas(1024) unsigned char stage[2][TC_STAGE_BYTES];
-    alignas(16) unsigned char raw[TC_MAXQ * TC_THREADS * 16];  // one tile of A and B as read
+    alignas(16) unsigned char raw[TC_RAW_CHUNKS * 16];  // one tile of A and B as read
     float acc_hi[128 * 128];  // [n][m]
     float acc_lo[128 * 128];
     alignas(8) uint64_t mbar[2];
@@ -263,11 +264,11 @@ k_gram_tc(int64_t n, const Ta *__restrict__ A, int lda, int ka, const Tb *__rest
             pending[st] = false;
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;");
-            // warp w reads lane quarter w % 4 (its own TMEM lanes), column slice w / 4
+            // warp w < 16 reads lane quarter w % 4 (its own TMEM lanes), column slice w / 4
             const int lane_m = (warp & 3) * 32 + (t & 31);
-            constexpr int CW = TC_COLS / (TC_WARPS / 4);  // columns per warp
+            constexpr int CW = TC_COLS / (TC_FOLD_WARPS / 4);  // columns per warp
 #pragma unroll 1
-            for (int c0 = (warp >> 2) * CW; c0 < ((warp >> 2) + 1) * CW; c0 += 32) {
+            for (int c0 = (warp >> 2) * CW; warp < TC_FOLD_WARPS && c0 < ((warp >> 2) + 1) * CW; c0 += 32) {
                 uint32_t v[32];
                 const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)c0;
                 asm volatile(
@@ -363,9 +364,9 @@ int gram_tc_pieces(sped_dtype at, sped_dtype bt, int ka, int kb, int lda, int ld
     const bool a_ok = at == SPED_F32 || at == SPED_BF16;
     const bool b_ok = kb == 0 || bt == SPED_F32 || bt == SPED_BF16;
     if (!a_ok || !b_ok) return 0;
-    // every thread holds at most TC_MAXQ 16-byte chunks of a tile
+    // one tile of A and B fits the raw buffer (TC_RAW_CHUNKS 16-byte chunks)
     const int ea = 16 / (int)dtype_size(at), eb = kb ? 16 / (int)dtype_size(bt) : 1;
-    if (TC_TILE * (lda / ea + (kb ? ldb / eb : 0)) > TC_MAXQ * TC_THREADS) return 0;
+    if (TC_TILE * (lda / ea + (kb ? ldb / eb : 0)) > TC_RAW_CHUNKS) return 0;
     const int S = (at == SPED_F32 || (kb > 0 && bt == SPED_F32)) ? 3 : 1;
     return S * (ka + kb) <= 128 ? S : 0;
 }
