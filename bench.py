@@ -67,9 +67,13 @@ def _peaks():
 
 
 def _kernel_source_hash():
+    """sha256 (first 16 hex digits) of the row-group chain kernel's source: spmm.cu up to its
+    merge-path section, then sped_internal.cuh."""
     h = hashlib.sha256()
-    for f in ["paper_2207_14589_gb300/csrc/spmm.cu", "paper_2207_14589_gb300/csrc/sped_internal.cuh"]:
-        h.update(open(os.path.join(ROOT, f), "rb").read())
+    spmm = open(os.path.join(ROOT, "paper_2207_14589_gb300/csrc/spmm.cu"), "rb").read()
+    cut = spmm.find(b"// merge path")
+    h.update(spmm[:cut] if cut >= 0 else spmm)
+    h.update(open(os.path.join(ROOT, "paper_2207_14589_gb300/csrc/sped_internal.cuh"), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -576,7 +580,7 @@ def run_ours(args, rank, world, local_rank):
         extra["differentiable"] = measure_differentiable(sped, torch, dev, stream)
         extra["batched"] = measure_batched(sped, torch, dev, stream)
     if rank == 0 and args.power_law:
-        extra["power_law"] = measure_power_law(sped, torch, dev, stream,
+        extra["power_law"] = measure_power_law(sped, torch, dev, stream, n=args.power_law_n,
                                                target_nnz=args.target_nnz)
     if rank == 0 and not args.no_ttk:
         # bottom-20 of this workload is not a well-conditioned subspace (Poisson low-degree
@@ -624,6 +628,8 @@ def main():
     ap.add_argument("--power-law", action="store_true",
                     help="also time the merge-path chain on the 16M-node Chung-Lu graph "
                          "(about 2 minutes of host-side graph generation)")
+    ap.add_argument("--power-law-n", type=int, default=16_000_000,
+                    help="nodes of the Chung-Lu graph for --power-law")
     ap.add_argument("--target-nnz", type=float, default=None,
                     help="scale the Chung-Lu expected degrees to this many stored entries")
     ap.add_argument("--spectrum", action="store_true",

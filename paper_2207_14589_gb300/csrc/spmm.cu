@@ -146,16 +146,29 @@ __device__ __forceinline__ void merge_search(int64_t diag, int n, int nnz,
     j = (int)(diag - lo);
 }
 
+// merge-path coordinates of every share boundary g * ipg (g = 0 .. n_groups), once per step
+__global__ void k_merge_coords(int64_t n_groups, int64_t ipg, int n, int nnz,
+                               const int32_t *__restrict__ rp, int2 *__restrict__ coords) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g > n_groups) return;
+    const int64_t total = (int64_t)n + nnz;
+    const int64_t d = g * ipg < total ? g * ipg : total;
+    int i, j;
+    merge_search(d, n, nnz, rp, i, j);
+    coords[g] = make_int2(i, j);
+}
+
 template <typename A> struct MergeParts {
     A *acc;        // [groups][2][KP]  (0 = head, 1 = tail)
     A *dsum;       // [groups][2]
     int32_t *row;  // [groups][2]      (-1 = none)
+    const int2 *coords;  // [groups + 1] merge-path coordinates of the share boundaries
     int KP;
 };
 
 template <typename Tx, typename Tv, typename Ty, typename A, bool W, bool HV>
 __global__ void __launch_bounds__(STEP_THREADS)
-k_step_merge(StepArgs<Tx, Tv, Ty, A, W, HV> a, int nnz, int groups_per_warp, int64_t ipg,
+k_step_merge(StepArgs<Tx, Tv, Ty, A, W, HV> a, int nnz, int groups_per_warp,
              int64_t n_groups, MergeParts<A> parts) {
     constexpr int E = 16 / (int)sizeof(Tx);
     const int lane = threadIdx.x & 31;
@@ -165,12 +178,8 @@ k_step_merge(StepArgs<Tx, Tv, Ty, A, W, HV> a, int nnz, int groups_per_warp, int
     if (gw >= groups_per_warp) return;
     const int64_t g = warp * groups_per_warp + gw;
     if (g >= n_groups) return;
-    const int64_t total = (int64_t)a.n + nnz;
-    const int64_t d0 = g * ipg;
-    const int64_t d1 = d0 + ipg < total ? d0 + ipg : total;
-    int i0, j0, i1, j1;
-    merge_search(d0, a.n, nnz, a.rp, i0, j0);
-    merge_search(d1, a.n, nnz, a.rp, i1, j1);
+    const int2 cs = parts.coords[g], ce = parts.coords[g + 1];
+    const int i0 = cs.x, j0 = cs.y, i1 = ce.x, j1 = ce.y;
     const Tx *Xc = a.X + c * E;
     A acc[E];
 #pragma unroll
@@ -210,24 +219,26 @@ k_step_merge(StepArgs<Tx, Tv, Ty, A, W, HV> a, int nnz, int groups_per_warp, int
         int jj[UNROLL];
 #pragma unroll
         for (int u = 0; u < UNROLL; ++u) jj[u] = __ldg(a.ci + p + u);
-        A x[UNROLL][E];
+        uint4 x[UNROLL];  // raw 16-byte chunks (E elements of Tx) until they are added
 #pragma unroll
-        for (int u = 0; u < UNROLL; ++u) load_chunk<Tx, E, A>(Xc + (int64_t)jj[u] * a.ldx, x[u]);
-        A wv[UNROLL];
+        for (int u = 0; u < UNROLL; ++u)
+            x[u] = __ldg(reinterpret_cast<const uint4 *>(Xc + (int64_t)jj[u] * a.ldx));
+        float wv[UNROLL];
         if constexpr (W) {
 #pragma unroll
-            for (int u = 0; u < UNROLL; ++u) wv[u] = (A)__ldg(a.w + p + u);
+            for (int u = 0; u < UNROLL; ++u) wv[u] = __ldg(a.w + p + u);
         }
 #pragma unroll
         for (int u = 0; u < UNROLL; ++u) {
             while (p + u >= rnext && i < i1) end_row();
+            const Tx *e = reinterpret_cast<const Tx *>(&x[u]);
             if constexpr (W) {
-                dsum += wv[u];
+                dsum += (A)wv[u];
 #pragma unroll
-                for (int q = 0; q < E; ++q) acc[q] += wv[u] * x[u][q];
+                for (int q = 0; q < E; ++q) acc[q] += (A)wv[u] * cvt<A>(e[q]);
             } else {
 #pragma unroll
-                for (int q = 0; q < E; ++q) acc[q] += x[u][q];
+                for (int q = 0; q < E; ++q) acc[q] += cvt<A>(e[q]);
             }
         }
     }
@@ -297,10 +308,18 @@ static bool use_merge(const sped_graph *g, int split) {
     return g->max_deg > 128 && g->max_deg > 8.0 * avg;
 }
 
+// Items (row ends + stored entries) per merge-path share. Shares are taken in order by
+// consecutive lane groups and CTAs are dispatched in index order, so the rows being worked on
+// at any moment form a window of about (resident groups x share) items; a short share keeps
+// that window's gather source inside L2 on graphs whose nodes are ordered by cluster.
+#ifndef SPED_MERGE_IPG
+#define SPED_MERGE_IPG 256
+#endif
+
 struct MergePlan {
     int64_t ipg, n_groups;
     int KP;
-    size_t acc_bytes, dsum_bytes, row_bytes;
+    size_t acc_bytes, dsum_bytes, row_bytes, coord_bytes;
 };
 
 static MergePlan merge_plan(const sped_graph *g, int k, sped_dtype xt, size_t acc_size) {
@@ -308,16 +327,13 @@ static MergePlan merge_plan(const sped_graph *g, int k, sped_dtype xt, size_t ac
     int E = chunk_elems(xt);
     int C = (k + E - 1) / E;
     int64_t total = g->n + g->nnz;
-    int64_t lanes = (int64_t)device_sm_count() * 2048;
-    int64_t target_groups = lanes / C * 2;
-    int64_t ipg = (total + target_groups - 1) / (target_groups > 0 ? target_groups : 1);
-    if (ipg < 32) ipg = 32;
-    m.ipg = ipg;
-    m.n_groups = (total + ipg - 1) / ipg;
+    m.ipg = SPED_MERGE_IPG;
+    m.n_groups = (total + m.ipg - 1) / m.ipg;
     m.KP = C * E;
     m.acc_bytes = (size_t)m.n_groups * 2 * m.KP * acc_size;
     m.dsum_bytes = (size_t)m.n_groups * 2 * acc_size;
     m.row_bytes = (size_t)m.n_groups * 2 * sizeof(int32_t);
+    m.coord_bytes = (size_t)(m.n_groups + 1) * sizeof(int2);
     return m;
 }
 
@@ -330,6 +346,7 @@ size_t poly_step_scratch(const sped_graph *g, int k, sped_dtype xt, int split) {
     p.add(m.acc_bytes);
     p.add(m.dsum_bytes);
     p.add(m.row_bytes);
+    p.add(m.coord_bytes);
     return p.total();
 }
 
@@ -371,13 +388,18 @@ static sped_status run_step(const sped_graph *g, int k, const void *X, int ldx, 
     parts.acc = (A *)scr.take(m.acc_bytes);
     parts.dsum = (A *)scr.take(m.dsum_bytes);
     parts.row = (int32_t *)scr.take(m.row_bytes);
+    int2 *coords = (int2 *)scr.take(m.coord_bytes);
+    parts.coords = coords;
     parts.KP = m.KP;
-    if (!parts.acc || !parts.dsum || !parts.row)
+    if (!parts.acc || !parts.dsum || !parts.row || !coords)
         return fail(SPED_ERR_SCRATCH, "poly_step (merge path): scratch too small");
+    k_merge_coords<<<(unsigned)((m.n_groups + 1 + 255) / 256), 256, 0, st>>>(
+        m.n_groups, m.ipg, (int)g->n, (int)g->nnz, g->rp, coords);
+    SPED_CHECK_LAUNCH("k_merge_coords");
     int64_t warps = (m.n_groups + per_warp - 1) / per_warp;
     int64_t blocks = (warps * 32 + STEP_THREADS - 1) / STEP_THREADS;
     k_step_merge<Tx, Tv, Ty, A, W, HV><<<(unsigned)blocks, STEP_THREADS, 0, st>>>(
-        a, (int)g->nnz, per_warp, m.ipg, m.n_groups, parts);
+        a, (int)g->nnz, per_warp, m.n_groups, parts);
     SPED_CHECK_LAUNCH("k_step_merge");
     k_merge_fixup<Tx, Tv, Ty, A, W, HV><<<(unsigned)blocks, STEP_THREADS, 0, st>>>(
         a, per_warp, m.n_groups, parts);
