@@ -68,12 +68,15 @@ def _peaks():
 
 def _kernel_source_hash():
     """sha256 (first 16 hex digits) of the row-group chain kernel's source: spmm.cu up to its
-    merge-path section, then sped_internal.cuh."""
+    merge-path section, then the device helpers of sped_internal.cuh (element conversions and
+    chunk loads / stores)."""
     h = hashlib.sha256()
     spmm = open(os.path.join(ROOT, "paper_2207_14589_gb300/csrc/spmm.cu"), "rb").read()
     cut = spmm.find(b"// merge path")
     h.update(spmm[:cut] if cut >= 0 else spmm)
-    h.update(open(os.path.join(ROOT, "paper_2207_14589_gb300/csrc/sped_internal.cuh"), "rb").read())
+    hdr = open(os.path.join(ROOT, "paper_2207_14589_gb300/csrc/sped_internal.cuh"), "rb").read()
+    a, b = hdr.find(b"// device helpers"), hdr.find(b"// Philox4x32-10")
+    h.update(hdr[a:b] if 0 <= a < b else hdr)
     return h.hexdigest()[:16]
 
 
@@ -440,9 +443,10 @@ def measure_power_law(sped, torch, dev, stream, n=16_000_000, k=32, ell=251, tar
     one_b = spmm_bytes(g.n, g.nnz, k, 2, 2, weighted=True) + 4 * g.n
     out = {"workload": f"chung_lu_n{g.n}_nnz{g.nnz}_k{k}_weighted", "n": g.n, "nnz": g.nnz,
            "max_degree": int(np.max(np.diff(g.row_ptr))), "k": k, "degree_l": ell,
-           "scale_s": info.scale_s, "host_generation_s": gen_s, "bytes_per_step": one_b}
+           "scale_s": info.scale_s, "host_generation_s": gen_s, "bytes_per_step": one_b,
+           "autotune": G.autotune(k, torch.bfloat16)}
     peak, kind = _peaks()
-    for split, name in ((2, "merge_path"), (1, "row_group")):
+    for split, name in ((0, "tuned"), (2, "merge_path"), (1, "row_group")):
         step = lambda: sped.poly_step(G, X, Y, k, alpha=0.0, beta=-info.scale_s, gamma=1.0,
                                       split=split)
         step()

@@ -146,6 +146,36 @@ sped_status sped_poly_step_scratch_size(const sped_graph *g, int k, sped_dtype x
                                         size_t *bytes);
 
 /* ------------------------------------------------------------------------------------
+ * Schedule selection for the chain step (the paper has no counterpart: it names no kernel).
+ * sped_autotune times one step X -> X - 0.01 L X of storage type chain_t on this graph for
+ * each candidate schedule -- the row-group kernel, and the merge path with shares of 128,
+ * 256, 512 and 1024 items (rows + stored entries) -- and records the fastest in the graph, so
+ * that every later split = 0 (automatic) step on it uses that schedule. The choice is also kept
+ * in a per-process table keyed by the graph's shape (n, nnz, maximum degree, weighted or not,
+ * k, chain_t, device); a later call for the same shape takes it from there without timing
+ * (report->cached = 1). The call synchronises `stream` (it reads CUDA event times).
+ * Scratch (device, 256-byte aligned): sped_autotune_scratch_size bytes; its contents are
+ * overwritten. Scratch needs of sped_poly_step / sped_apply_poly / sped_eig_step depend on the
+ * chosen schedule, so query them after tuning. On failure the graph keeps its previous
+ * schedule. sped_set_schedule fixes it by hand (split 0 = degree rule, 1 = row group,
+ * 2 = merge path; merge_ipg 0 = default share, else 32..2^20 items).
+ * ------------------------------------------------------------------------------------ */
+typedef struct {
+    int split;         /* chosen schedule: 1 row group, 2 merge path                          */
+    int merge_ipg;     /* merge-path share in items when split == 2, else 0                   */
+    int cached;        /* 1: taken from the per-process table, nothing was timed              */
+    int n_candidates;  /* entries of ms[] filled                                               */
+    double ms[8];      /* mean step time per candidate: [0] row group, [1..4] merge path with
+                          shares 128, 256, 512, 1024                                           */
+} sped_tune_report;
+
+sped_status sped_autotune_scratch_size(const sped_graph *g, int k, sped_dtype chain_t,
+                                       size_t *bytes);
+sped_status sped_autotune(sped_graph *g, int k, sped_dtype chain_t, void *d_scratch,
+                          size_t scratch_bytes, void *stream, sped_tune_report *report);
+sped_status sped_set_schedule(sped_graph *g, int split, int merge_ipg);
+
+/* ------------------------------------------------------------------------------------
  * Y = M V for the graph's polynomial M (Sections 4.2-4.3).
  *  mode SPED_EXACT: the chain of poly steps; intermediate products stored as chain_t
  *    (BF16 halves gather traffic, accumulation stays F32), the last step writes y_t.

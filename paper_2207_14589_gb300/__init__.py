@@ -61,6 +61,11 @@ class sped_solve_opts(ctypes.Structure):
                 ("refine_chain_t", ctypes.c_int)]
 
 
+class sped_tune_report(ctypes.Structure):
+    _fields_ = [("split", ctypes.c_int), ("merge_ipg", ctypes.c_int), ("cached", ctypes.c_int),
+                ("n_candidates", ctypes.c_int), ("ms", ctypes.c_double * 8)]
+
+
 class sped_solve_report(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int), ("phase1_steps", ctypes.c_int),
                 ("spmm_count", ctypes.c_int64), ("final_residual", ctypes.c_double),
@@ -106,6 +111,9 @@ def lib():
         "sped_solve_scratch_size": [vp, P(sped_solve_opts), i32, P(sz)],
         "sped_cluster_assign": [vp, i32, i64, i32, i32, i32, u64, i32, vp, P(i32), vp, sz, vp],
         "sped_cluster_scratch_size": [i64, i32, i32, P(sz)],
+        "sped_autotune_scratch_size": [vp, i32, i32, P(sz)],
+        "sped_autotune": [vp, i32, i32, vp, sz, vp, P(sped_tune_report)],
+        "sped_set_schedule": [vp, i32, i32],
     }
     for name, args in sigs.items():
         f = getattr(L, name)
@@ -246,6 +254,21 @@ class Graph:
         _check(lib().sped_set_polynomial(self.handle, kind, degree, float(scale), float(eps),
                                          c, float(lambda_star)))
         return self.info()
+
+    def autotune(self, k, chain_dtype=torch.bfloat16, stream=None):
+        """Time the chain-step schedules on this graph and keep the fastest (sped_autotune)."""
+        ct = _TORCH_DT[chain_dtype]
+        nb = ctypes.c_size_t()
+        _check(lib().sped_autotune_scratch_size(self.handle, k, ct, ctypes.byref(nb)))
+        scr = _scratch(nb.value, self.device)
+        rep = sped_tune_report()
+        _check(lib().sped_autotune(self.handle, k, ct, _ptr(scr), nb.value, _stream(stream),
+                                   ctypes.byref(rep)))
+        return {"split": rep.split, "merge_ipg": rep.merge_ipg, "cached": bool(rep.cached),
+                "ms": list(rep.ms[:rep.n_candidates])}
+
+    def set_schedule(self, split=0, merge_ipg=0):
+        _check(lib().sped_set_schedule(self.handle, int(split), int(merge_ipg)))
 
     def power_coeffs(self):
         d = self.info().degree

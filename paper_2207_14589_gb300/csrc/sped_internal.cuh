@@ -110,6 +110,9 @@ struct sped_graph {
     double max_wdeg;
     double lambda_bound;
     sped::Poly poly;
+    int32_t tuned_split;  // chain-step schedule chosen by sped_autotune: 0 none (degree rule),
+                          // 1 row group, 2 merge path
+    int32_t merge_ipg;    // merge-path share in items (rows + entries); 0 = default
 };
 
 namespace sped {
@@ -278,6 +281,7 @@ sped_status launch_poly_step(const sped_graph *g, int k, const void *X, sped_dty
                              double alpha, double beta, double gamma, int split, Scratch &scr,
                              cudaStream_t st);
 size_t poly_step_scratch(const sped_graph *g, int k, sped_dtype xt, int split);
+size_t merge_step_scratch(const sped_graph *g, int k, sped_dtype xt, int ipg);
 sped_status launch_gram(int64_t n, const void *A, sped_dtype at, int lda, int ka, const void *B,
                         sped_dtype bt, int ldb, int kb, double *G, Scratch &scr, cudaStream_t st);
 size_t gram_scratch(int64_t n, int ka, int kb);

@@ -304,17 +304,17 @@ k_merge_fixup(StepArgs<Tx, Tv, Ty, A, W, HV> a, int groups_per_warp, int64_t n_g
 static bool use_merge(const sped_graph *g, int split) {
     if (split == 1) return false;
     if (split == 2) return true;
+    if (g->tuned_split) return g->tuned_split == 2;
     double avg = g->n ? (double)g->nnz / (double)g->n : 0.0;
     return g->max_deg > 128 && g->max_deg > 8.0 * avg;
 }
 
-// Items (row ends + stored entries) per merge-path share. Shares are taken in order by
-// consecutive lane groups and CTAs are dispatched in index order, so the rows being worked on
-// at any moment form a window of about (resident groups x share) items; a short share keeps
-// that window's gather source inside L2 on graphs whose nodes are ordered by cluster.
-#ifndef SPED_MERGE_IPG
-#define SPED_MERGE_IPG 256
-#endif
+// Items (row ends + stored entries) per merge-path share, unless sped_autotune chose another.
+// Shares are taken in order by consecutive lane groups and CTAs are dispatched in index order,
+// so the rows being worked on at any moment form a window of about (resident groups x share)
+// items; a short share keeps that window's gather source inside L2 on graphs whose nodes are
+// ordered by cluster, at the price of more partial rows for the fix-up.
+constexpr int MERGE_IPG_DEFAULT = 256;
 
 struct MergePlan {
     int64_t ipg, n_groups;
@@ -327,7 +327,7 @@ static MergePlan merge_plan(const sped_graph *g, int k, sped_dtype xt, size_t ac
     int E = chunk_elems(xt);
     int C = (k + E - 1) / E;
     int64_t total = g->n + g->nnz;
-    m.ipg = SPED_MERGE_IPG;
+    m.ipg = g->merge_ipg > 0 ? g->merge_ipg : MERGE_IPG_DEFAULT;
     m.n_groups = (total + m.ipg - 1) / m.ipg;
     m.KP = C * E;
     m.acc_bytes = (size_t)m.n_groups * 2 * m.KP * acc_size;
@@ -338,6 +338,20 @@ static MergePlan merge_plan(const sped_graph *g, int k, sped_dtype xt, size_t ac
 }
 
 static size_t acc_size_for(sped_dtype yt) { return yt == SPED_F64 ? 8 : 4; }
+
+size_t merge_step_scratch(const sped_graph *g, int k, sped_dtype xt, int ipg) {
+    sped_graph probe_shape;  // only n, nnz and the share size enter the plan
+    probe_shape.n = g->n;
+    probe_shape.nnz = g->nnz;
+    probe_shape.merge_ipg = ipg;
+    MergePlan m = merge_plan(&probe_shape, k, xt, 8);
+    ScratchPlan p;
+    p.add(m.acc_bytes);
+    p.add(m.dsum_bytes);
+    p.add(m.row_bytes);
+    p.add(m.coord_bytes);
+    return p.total();
+}
 
 size_t poly_step_scratch(const sped_graph *g, int k, sped_dtype xt, int split) {
     if (!use_merge(g, split)) return 0;
@@ -393,6 +407,7 @@ static sped_status run_step(const sped_graph *g, int k, const void *X, int ldx, 
     parts.KP = m.KP;
     if (!parts.acc || !parts.dsum || !parts.row || !coords)
         return fail(SPED_ERR_SCRATCH, "poly_step (merge path): scratch too small");
+    if (m.n_groups == 0) return SPED_OK;
     k_merge_coords<<<(unsigned)((m.n_groups + 1 + 255) / 256), 256, 0, st>>>(
         m.n_groups, m.ipg, (int)g->n, (int)g->nnz, g->rp, coords);
     SPED_CHECK_LAUNCH("k_merge_coords");
