@@ -5,20 +5,29 @@
 // recover x_i x_j to F32 accuracy. The pieces are stacked as S*K2 <= 128 operand rows (S = 3
 // for F32 inputs, 1 for BF16) and one tcgen05.mma (M = N = 128, K = 16 graph rows, kind::f16
 // with BF16 operands, F32 accumulator in tensor memory) consumes 16 rows; the same
-// shared-memory tile is both operands because G is a Gram matrix. 128 graph rows form a tile;
-// two tiles are in flight (a tcgen05.commit per tile signals its mbarrier). Every few tiles
-// the accumulator is read back with tcgen05.ld and added to double-float (two F32) sums in
-// shared memory, bounding the F32 accumulation to a short run of rows. At the end the nine
-// piece blocks are combined per (i, j) and the CTA writes an F64 partial; a second kernel
-// sums the partials in a fixed order.
+// shared-memory tile is both operands because G is a Gram matrix.
+//
+// Pipeline per CTA (one per SM, tiles of 128 graph rows taken round-robin):
+//  * thread 0 keeps NRAW - 1 tiles of raw rows in flight: one bulk copy (cp.async.bulk) of the
+//    tile's contiguous rows of A and one of B into a raw stage, completion counted in bytes on
+//    the stage's mbarrier; a stage is refilled once every warp has arrived on its "empty"
+//    barrier;
+//  * all warps split the raw stage into the K-major core-matrix layout of an operand stage
+//    (two operand stages, one per MMA batch in flight);
+//  * thread 0 issues the tile's 8 MMAs and a tcgen05.commit to the operand stage's mbarrier;
+//  * every 4 tiles the accumulator is read back and added to double-float (TwoSum) running
+//    sums that live in spare tensor-memory columns (the accumulator uses 128 of 512), bounding
+//    each F32 accumulation to 512 rows.
+// At the end the running sums go to shared memory, the nine piece blocks are combined per
+// (i, j) and the CTA writes an F64 partial; a second kernel sums the partials in a fixed order.
 //
 // Shared-memory operand layout (no swizzle, K-major): per 16-row slice a 128 x 16 BF16 block
 // made of 8 x 8 core matrices (128 contiguous bytes each); core matrix (g = m/8, h = k/8) at
 // byte (2g + h) * 128, so the K-adjacent core matrix is 128 bytes away (leading byte offset)
 // and the next 8-row group 256 bytes away (stride byte offset).
 //
-// Every wait is bounded: if a tile's completion is not observed within the limit the CTA
-// stops issuing work, waits (bounded) for what it issued, releases its tensor memory and
+// Every wait is bounded: if a completion is not observed within the limit the CTA stops issuing
+// work, waits (bounded) for the copies and MMAs it issued, releases its tensor memory and
 // writes NaN partials, so the caller sees a non-finite Gram instead of a hang.
 #include <cmath>
 
@@ -27,27 +36,35 @@
 namespace sped {
 
 constexpr int TC_THREADS = 640;       // 20 warps: one split unit per thread at k = 20 (K2 = 40)
+constexpr int TC_WARPS = TC_THREADS / 32;
 constexpr int TC_RAW_CHUNKS = 2048;   // 16-byte chunks of one tile of A and B at most
-constexpr int TC_MAXQ = (TC_RAW_CHUNKS + TC_THREADS - 1) / TC_THREADS;  // per thread
-constexpr int TC_FOLD_WARPS = 16;     // warps that read the accumulator (4 per TMEM lane quarter)
+constexpr int TC_RAW_BYTES = TC_RAW_CHUNKS * 16;
+constexpr int TC_NRAW = 3;            // raw stages: two tiles' copies in flight during a split
+constexpr int TC_FOLD_WARPS = 16;     // warps that read tensor memory (4 per TMEM lane quarter)
 constexpr int TC_TILE = 128;          // graph rows per tile
 constexpr int TC_SLICES = TC_TILE / 16;
 constexpr int TC_SLICE_BYTES = 128 * 16 * 2;
 constexpr int TC_STAGE_BYTES = TC_SLICES * TC_SLICE_BYTES;  // 32 KB
 constexpr int TC_FLUSH = 4;           // tiles per F32 accumulation run
-constexpr int TC_COLS = 128;          // tensor-memory columns (N)
+constexpr int TC_COLS = 128;          // accumulator columns (N)
+constexpr int TC_HI = 128, TC_LO = 256;  // tensor-memory columns of the running sums
+constexpr int TC_TMEM_COLS = 512;     // allocation (power of two >= 384)
 constexpr uint32_t TC_WAIT_LIMIT = 1u << 22;
 
 struct TcSmem {
+    // the operand stages and the raw stages are contiguous: at the end they hold the running
+    // sums read out of tensor memory (2 x 64 KB)
     alignas(1024) unsigned char stage[2][TC_STAGE_BYTES];
-    alignas(16) unsigned char raw[TC_RAW_CHUNKS * 16];  // one tile of A and B as read
-    float acc_hi[128 * 128];  // [n][m]
-    float acc_lo[128 * 128];
-    alignas(8) uint64_t mbar[2];
+    alignas(128) unsigned char raw[TC_NRAW][TC_RAW_BYTES];
+    alignas(8) uint64_t mma_bar[2];
+    alignas(8) uint64_t full_bar[TC_NRAW];
+    alignas(8) uint64_t empty_bar[TC_NRAW];
     uint32_t tmem_base;
     int timed_out;
     int wait_ok;
 };
+static_assert(sizeof(TcSmem::stage) + sizeof(TcSmem::raw) >= 2 * 128 * 128 * sizeof(float),
+              "final staging of the running sums");
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -103,13 +120,48 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
     return false;
 }
 
-// CTA-uniform bounded wait: thread 0 polls, every thread gets the same answer
-__device__ __forceinline__ bool cta_wait(uint32_t mbar, uint32_t parity, int *flag) {
-    if (threadIdx.x == 0) *flag = mbar_wait(mbar, parity) ? 1 : 0;
-    __syncthreads();
-    const bool r = *flag != 0;
-    __syncthreads();
-    return r;
+__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes)
+                 : "memory");
+}
+
+// bulk copy global -> shared (16-byte aligned ends, size a multiple of 16), completion counted
+// in bytes on mbar
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes,
+                                         uint32_t mbar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(dst), "l"(src), "r"(bytes), "r"(mbar)
+        : "memory");
+}
+
+// 32 lanes x 16 columns of tensor memory, one 32-bit value per (lane, column)
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+          "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+        "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
+        ::"r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]),
+          "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]),
+          "r"(v[13]), "r"(v[14]), "r"(v[15])
+        : "memory");
 }
 
 __device__ __forceinline__ void two_sum(float &s, float &e, float x) {
@@ -126,87 +178,110 @@ k_gram_tc(int64_t n, const Ta *__restrict__ A, int lda, int ka, const Tb *__rest
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     TcSmem &sm = *reinterpret_cast<TcSmem *>(
         smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023));
-    constexpr int EA = 16 / (int)sizeof(Ta), EB = 16 / (int)sizeof(Tb);
     const int t = threadIdx.x;
-    const int warp = t >> 5;
+    const int warp = t >> 5, lane = t & 31;
     const int K2 = ka + kb;
     const int c_first = t % K2, g_first = t / K2;                 // this thread's first split unit
     const int c_step = TC_THREADS % K2, g_step = TC_THREADS / K2;  // and the stride between units
-    // ---- set-up: zero operands and sums, barriers, tensor memory
+    const int64_t ntiles = (n + TC_TILE - 1) / TC_TILE;
+    const int64_t my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    // ---- set-up: zero the operand stages (rows past S K2 stay zero), barriers, tensor memory
     for (int e = t; e < 2 * TC_STAGE_BYTES / 16; e += TC_THREADS)
         reinterpret_cast<uint4 *>(&sm.stage[0][0])[e] = make_uint4(0, 0, 0, 0);
-    for (int e = t; e < 128 * 128; e += TC_THREADS) {
-        sm.acc_hi[e] = 0.f;
-        sm.acc_lo[e] = 0.f;
-    }
     if (t == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sm.mbar[0])));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sm.mbar[1])));
+        for (int i = 0; i < 2; ++i) mbar_init(smem_u32(&sm.mma_bar[i]), 1);
+        for (int i = 0; i < TC_NRAW; ++i) {
+            mbar_init(smem_u32(&sm.full_bar[i]), 1);
+            mbar_init(smem_u32(&sm.empty_bar[i]), TC_WARPS);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         sm.timed_out = 0;
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&sm.tmem_base)),
-                     "r"(TC_COLS));
+                     "r"(TC_TMEM_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = sm.tmem_base;
+    // warp w < 16 owns TMEM lane quarter w % 4 and accumulator columns [32 (w / 4), +32)
+    const bool folder = warp < TC_FOLD_WARPS;
+    const uint32_t lane_q = (uint32_t)((warp & 3) * 32) << 16;
+    const int col0 = (warp >> 2) * 32;
+    if (folder) {  // running sums start at zero
+        uint32_t z[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) z[q] = 0u;
+#pragma unroll
+        for (int h = 0; h < 32; h += 16) {
+            tmem_st16(tmem + lane_q + (uint32_t)(TC_HI + col0 + h), z);
+            tmem_st16(tmem + lane_q + (uint32_t)(TC_LO + col0 + h), z);
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    }
     const uint32_t idesc = tc_idesc();
-    uint32_t parity[2] = {0, 0};
+    // raw tile loads (thread 0): fill number f of raw stage f % NRAW holds this CTA's tile f
+    int64_t issued = 0;
+    auto issue = [&]() {  // next fill, once its stage has been released by every warp
+        const int64_t f = issued;
+        if (f >= my_tiles) return true;
+        const int rs = (int)(f % TC_NRAW);
+        if (f >= TC_NRAW &&
+            !mbar_wait(smem_u32(&sm.empty_bar[rs]), (uint32_t)(((f / TC_NRAW) - 1) & 1)))
+            return false;
+        const int64_t r0 = (blockIdx.x + f * gridDim.x) * (int64_t)TC_TILE;
+        const int rows = (int)(n - r0 < TC_TILE ? n - r0 : TC_TILE);
+        const uint32_t ba = (uint32_t)((size_t)rows * lda * sizeof(Ta));
+        const uint32_t bb = (uint32_t)((size_t)rows * ldb * sizeof(Tb));
+        const uint32_t bar = smem_u32(&sm.full_bar[rs]);
+        mbar_arrive_expect_tx(bar, ba + bb);
+        bulk_g2s(smem_u32(sm.raw[rs]), A + r0 * lda, ba, bar);
+        if (bb) bulk_g2s(smem_u32(sm.raw[rs]) + ba, B + r0 * ldb, bb, bar);
+        ++issued;
+        return true;
+    };
+    if (t == 0) {
+        for (int f = 0; f < TC_NRAW - 1; ++f)
+            if (!issue()) sm.timed_out = 1;
+    }
+    uint32_t mma_par[2] = {0, 0};
     bool pending[2] = {false, false};
     bool fresh = true;  // next MMA overwrites the accumulator
     bool ok = true;
-    const int64_t ntiles = (n + TC_TILE - 1) / TC_TILE;
-    // the 16-byte chunks of the next two tiles held by this thread (two tiles in flight)
-    uint4 buf[TC_MAXQ], buf2[TC_MAXQ];
-    auto load_tile = [&](int64_t tl, uint4 (&dst)[TC_MAXQ]) {
-        if (tl >= ntiles) return;
-        const int64_t q0 = tl * TC_TILE;
-        const int rws = (int)(n - q0 < TC_TILE ? n - q0 : TC_TILE);
-        const int na = rws * lda / EA, nb = rws * ldb / EB;
-#pragma unroll
-        for (int u = 0; u < TC_MAXQ; ++u) {
-            const int q = t + u * TC_THREADS;
-            if (q < na) dst[u] = __ldg(reinterpret_cast<const uint4 *>(A + q0 * lda) + q);
-            else if (q - na < nb) dst[u] = __ldg(reinterpret_cast<const uint4 *>(B + q0 * ldb) + (q - na));
-        }
-    };
-    load_tile(blockIdx.x, buf);
-    load_tile(blockIdx.x + gridDim.x, buf2);
-    int it = 0;
-    for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it) {
-        const int st = it & 1;
-        if (pending[st]) {  // MMAs of the tile that last used this stage have read it
-            ok = cta_wait(smem_u32(&sm.mbar[st]), parity[st], &sm.wait_ok);
-            parity[st] ^= 1;
-            pending[st] = false;
-            if (!ok) break;
-        }
-        // ---- stage: the tile's rows of A and B are contiguous (row stride lda / ldb); the CTA
-        // read them as 16-byte chunks in address order two tiles ahead and now parks them in
-        // shared memory as they are
-        const int64_t r0 = tile * TC_TILE;
-        const int rows = (int)(n - r0 < TC_TILE ? n - r0 : TC_TILE);
-        const int qa = rows * lda / EA, qb = rows * ldb / EB;  // chunks of A and of B
-#pragma unroll
-        for (int u = 0; u < TC_MAXQ; ++u) {
-            const int q = t + u * TC_THREADS;
-            if (q < qa + qb) reinterpret_cast<uint4 *>(sm.raw)[q] = buf[u];
+    for (int64_t it = 0; it < my_tiles && ok; ++it) {
+        const int64_t tile = blockIdx.x + it * gridDim.x;
+        const int st = (int)(it & 1);
+        const int rs = (int)(it % TC_NRAW);
+        // ---- thread 0: keep NRAW - 1 fills ahead, then wait for this tile's rows and for the
+        // MMAs that last read this operand stage; every thread gets the same answer
+        if (t == 0) {
+            bool good = sm.timed_out == 0;
+            if (good && issued < my_tiles && !issue()) good = false;
+            if (good && !mbar_wait(smem_u32(&sm.full_bar[rs]), (uint32_t)((it / TC_NRAW) & 1)))
+                good = false;
+            if (good && pending[st] && !mbar_wait(smem_u32(&sm.mma_bar[st]), mma_par[st]))
+                good = false;
+            if (!good) sm.timed_out = 1;
+            sm.wait_ok = good ? 1 : 0;
         }
         __syncthreads();
-#pragma unroll
-        for (int u = 0; u < TC_MAXQ; ++u) buf[u] = buf2[u];
-        load_tile(tile + 2 * (int64_t)gridDim.x, buf2);  // flies during two splits and MMAs
+        ok = sm.wait_ok != 0;
+        if (!ok) break;
+        if (pending[st]) {
+            mma_par[st] ^= 1;
+            pending[st] = false;
+        }
         // ---- split: unit (c, g) is column c of [A B] over graph rows 8g .. 8g+7 (zero past the
         // end); each of its S BF16 pieces is 8 consecutive K elements, i.e. one 16-byte row of
         // a core matrix (operand row m = s K2 + c, K half g & 1 of slice g / 2)
+        const int64_t r0 = tile * TC_TILE;
+        const int rows = (int)(n - r0 < TC_TILE ? n - r0 : TC_TILE);
         {
-            const Ta *ra = reinterpret_cast<const Ta *>(sm.raw);
-            const Tb *rb = reinterpret_cast<const Tb *>(sm.raw + (size_t)qa * 16);
+            const Ta *ra = reinterpret_cast<const Ta *>(sm.raw[rs]);
+            const Tb *rb = reinterpret_cast<const Tb *>(sm.raw[rs] + (size_t)rows * lda * sizeof(Ta));
             // unit uu = g K2 + c, advanced by TC_THREADS without a division per unit
             int c = c_first, g = g_first;
             for (; g < TC_TILE / 8; c += c_step, g += g_step) {
@@ -242,6 +317,8 @@ k_gram_tc(int64_t n, const Ta *__restrict__ A, int lda, int ka, const Tb *__rest
                 }
             }
         }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&sm.empty_bar[rs]));  // raw stage may be refilled
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (t == 0) {
@@ -252,79 +329,104 @@ k_gram_tc(int64_t n, const Ta *__restrict__ A, int lda, int ka, const Tb *__rest
                 const uint64_t d = tc_desc(sbase + s * TC_SLICE_BYTES);
                 tc_mma(tmem, d, d, idesc, (fresh && s == 0) ? 0u : 1u);
             }
-            tc_commit(smem_u32(&sm.mbar[st]));
+            tc_commit(smem_u32(&sm.mma_bar[st]));
         }
         fresh = false;
         pending[st] = true;
-        const bool last = tile + gridDim.x >= ntiles;
-        if ((it + 1) % TC_FLUSH == 0 || last) {
-            // ---- fold the accumulator into the double-float sums
-            ok = cta_wait(smem_u32(&sm.mbar[st]), parity[st], &sm.wait_ok);
-            parity[st] ^= 1;
-            pending[st] = false;
+        if ((it + 1) % TC_FLUSH == 0 || it + 1 == my_tiles) {
+            // ---- fold the accumulator into the double-float running sums in tensor memory
+            if (t == 0) {
+                const bool good = mbar_wait(smem_u32(&sm.mma_bar[st]), mma_par[st]);
+                if (!good) sm.timed_out = 1;
+                sm.wait_ok = good ? 1 : 0;
+            }
+            __syncthreads();
+            ok = sm.wait_ok != 0;
             if (!ok) break;
+            mma_par[st] ^= 1;
+            pending[st] = false;
             asm volatile("tcgen05.fence::after_thread_sync;");
-            // warp w < 16 reads lane quarter w % 4 (its own TMEM lanes), column slice w / 4
-            const int lane_m = (warp & 3) * 32 + (t & 31);
-            constexpr int CW = TC_COLS / (TC_FOLD_WARPS / 4);  // columns per warp
+            if (folder) {
 #pragma unroll 1
-            for (int c0 = (warp >> 2) * CW; warp < TC_FOLD_WARPS && c0 < ((warp >> 2) + 1) * CW; c0 += 32) {
-                uint32_t v[32];
-                const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)c0;
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-                    "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
-                      "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
-                      "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
-                      "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
-                      "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]),
-                      "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-                    : "r"(taddr));
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                for (int h = 0; h < 32; h += 16) {
+                    uint32_t v[16], hi[16], lo[16];
+                    tmem_ld16(tmem + lane_q + (uint32_t)(col0 + h), v);
+                    tmem_ld16(tmem + lane_q + (uint32_t)(TC_HI + col0 + h), hi);
+                    tmem_ld16(tmem + lane_q + (uint32_t)(TC_LO + col0 + h), lo);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-                for (int q = 0; q < 32; ++q) {
-                    const int idx = (c0 + q) * 128 + lane_m;  // [n][m], m = this thread's lane
-                    float s = sm.acc_hi[idx], e = sm.acc_lo[idx];
-                    two_sum(s, e, __uint_as_float(v[q]));
-                    sm.acc_hi[idx] = s;
-                    sm.acc_lo[idx] = e;
+                    for (int q = 0; q < 16; ++q) {
+                        float sh = __uint_as_float(hi[q]), el = __uint_as_float(lo[q]);
+                        two_sum(sh, el, __uint_as_float(v[q]));
+                        hi[q] = __float_as_uint(sh);
+                        lo[q] = __float_as_uint(el);
+                    }
+                    tmem_st16(tmem + lane_q + (uint32_t)(TC_HI + col0 + h), hi);
+                    tmem_st16(tmem + lane_q + (uint32_t)(TC_LO + col0 + h), lo);
                 }
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
             }
             asm volatile("tcgen05.fence::before_thread_sync;");
             fresh = true;
         }
-        __syncthreads();
     }
-    // ---- on a timeout, wait (bounded) for whatever is still in flight
+    // ---- on a timeout, wait (bounded) for whatever is still in flight: MMAs, raw copies
     if (t == 0) {
         if (!ok) sm.timed_out = 1;
         for (int s = 0; s < 2; ++s)
-            if (pending[s] && !mbar_wait(smem_u32(&sm.mbar[s]), parity[s])) sm.timed_out = 1;
+            if (pending[s] && !mbar_wait(smem_u32(&sm.mma_bar[s]), mma_par[s])) sm.timed_out = 2;
+        // fills issued but not consumed by the loop (only after a timeout)
+        if (!ok)
+            for (int64_t f = 0; f < issued; ++f)
+                if (!mbar_wait(smem_u32(&sm.full_bar[f % TC_NRAW]), (uint32_t)((f / TC_NRAW) & 1)))
+                    sm.timed_out = 2;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    // the running sums to shared memory ([n][m] layout), unless copies may still be landing
+    float *fin_hi = reinterpret_cast<float *>(&sm.stage[0][0]);
+    float *fin_lo = fin_hi + 128 * 128;
+    const int bad = sm.timed_out;
+    if (bad != 2 && folder) {
+#pragma unroll 1
+        for (int h = 0; h < 32; h += 16) {
+            uint32_t hi[16], lo[16];
+            tmem_ld16(tmem + lane_q + (uint32_t)(TC_HI + col0 + h), hi);
+            tmem_ld16(tmem + lane_q + (uint32_t)(TC_LO + col0 + h), lo);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            const int m = (warp & 3) * 32 + lane;
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                fin_hi[(col0 + h + q) * 128 + m] = __uint_as_float(hi[q]);
+                fin_lo[(col0 + h + q) * 128 + m] = __uint_as_float(lo[q]);
+            }
+        }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                     "r"(TC_COLS));
+                     "r"(TC_TMEM_COLS));
     // ---- combine the S x S piece blocks: G[i][j] = sum_{a,b} D[a K2 + i][b K2 + j], i <= j
-    const bool bad = sm.timed_out != 0;
     double *out = partial + (int64_t)blockIdx.x * K2 * K2;
     for (int e = t; e < K2 * K2; e += TC_THREADS) {
         const int i = e / K2, j = e % K2;
         if (i > j) continue;
-        float s = 0.f, err = 0.f;
+        double v = NAN;
+        if (!bad) {
+            float s = 0.f, err = 0.f;
 #pragma unroll
-        for (int a = 0; a < S; ++a)
+            for (int a = 0; a < S; ++a)
 #pragma unroll
-            for (int b = 0; b < S; ++b) {
-                const int idx = (b * K2 + j) * 128 + (a * K2 + i);
-                two_sum(s, err, sm.acc_hi[idx]);
-                err += sm.acc_lo[idx];
-            }
-        const double v = bad ? NAN : (double)s + (double)err;
+                for (int b = 0; b < S; ++b) {
+                    const int idx = (b * K2 + j) * 128 + (a * K2 + i);
+                    two_sum(s, err, fin_hi[idx]);
+                    err += fin_lo[idx];
+                }
+            v = (double)s + (double)err;
+        }
         out[i * K2 + j] = v;
         out[j * K2 + i] = v;
     }
