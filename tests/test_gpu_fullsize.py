@@ -18,15 +18,15 @@ N, BLOCKS, K, ELL = 1_000_000, 20, 20, 41
 
 
 @pytest.fixture(scope="module")
-def cfg2():
+def sbm_n1e6():
     g = gen.sbm(N, BLOCKS, 14 / 49_999, 2 / 950_000, seed=gen.DEFAULT_SEED)
     G = sped.Graph.from_csr(g)
     info = G.set_polynomial(sped.POLY_LIMIT_EXP, ELL)
     return g, G, info
 
 
-def test_chain_step_sampled_rows(cfg2):
-    g, G, info = cfg2
+def test_chain_step_sampled_rows(sbm_n1e6):
+    g, G, info = sbm_n1e6
     s = info.scale_s
     X0 = gen.gaussian_block(N, K, seed=3)
     X = to_block(X0, torch.bfloat16)
@@ -43,9 +43,9 @@ def test_chain_step_sampled_rows(cfg2):
     assert rel(got, want) <= 1e-5
 
 
-def test_chain_keeps_constant_vector(cfg2):
+def test_chain_keeps_constant_vector(sbm_n1e6):
     # L 1 = 0, so every step maps 1 to 1 exactly (BF16 storage, F32 accumulation)
-    g, G, info = cfg2
+    g, G, info = sbm_n1e6
     V = to_block(np.ones((N, K)), torch.float32)
     Y = sped.alloc_block(N, K, torch.float32, DEV)
     sped.apply_poly(G, V, Y, K, chain_dtype=torch.bfloat16)
@@ -62,9 +62,9 @@ def test_tensor_gram_full_size():
     assert rel(Gm, M.T @ M) <= 2e-6
 
 
-def test_mixed_eig_step_full_size(cfg2):
+def test_mixed_eig_step_full_size(sbm_n1e6):
     # one benchmark step (BF16 chain, F32 master, mu-EG eta = 1) against the oracle's FP64 step
-    g, G, info = cfg2
+    g, G, info = sbm_n1e6
     V0 = gen.gaussian_block(N, K, seed=7)
     V0 /= np.linalg.norm(V0, axis=0)
     V = to_block(V0, torch.float32)

@@ -85,13 +85,13 @@ def test_eig_step_mixed_precision_close_to_fp64():
     assert rel(host(V, k), want) <= 1e-2
 
 
-def _config1():
+def _sbm_n2000_k4():
     return gen.sbm(2000, 4, 0.05, 0.001, seed=gen.DEFAULT_SEED)
 
 
 @pytest.mark.parametrize("arm", ["plain_fp64", "dilated_fp64", "dilated_mixed", "dilated_oja"])
-def test_solve_bottom_k_config1(arm):
-    g = _config1()
+def test_solve_bottom_k_sbm_n2000_k4(arm):
+    g = _sbm_n2000_k4()
     G = sped.Graph.from_csr(g)
     k = 4
     lam, Ustar = oracle.bottom_k(g, k)
@@ -132,8 +132,8 @@ def test_solve_bottom_k_config1(arm):
                        rtol=1e-9, atol=1e-12)
 
 
-def test_cluster_assign_config1_labels_bit_exact():
-    g = _config1()
+def test_cluster_assign_sbm_n2000_k4_labels_bit_exact():
+    g = _sbm_n2000_k4()
     k = 4
     lam, U = oracle.bottom_k(g, k)
     for dtype in (torch.float64, torch.float32):
