@@ -347,6 +347,22 @@ def ritz_values(V, Y):
     return np.einsum("ni,ni->i", V, Y) / np.einsum("ni,ni->i", V, V)
 
 
+def rayleigh_ritz(g, V):
+    """Ritz pairs of L on span(V) (the Rayleigh-Ritz procedure): with R the upper Cholesky
+    factor of V^T V (so Q = V R^{-1} is an orthonormal basis of span(V)), the eigenpairs
+    (theta_i, z_i) of the symmetric k x k matrix Q^T L Q = R^{-T} (V^T L V) R^{-1}, theta
+    ascending. Returns theta and W = R^{-1} Z, so that the Ritz vectors are the columns of V W
+    (orthonormal)."""
+    V = np.asarray(V, dtype=np.float64)
+    P = V.T @ V
+    H = V.T @ laplacian_apply(g, V)
+    R = np.linalg.cholesky(P).T
+    Ri = np.linalg.solve(R, np.eye(R.shape[0]))
+    Hs = Ri.T @ H @ Ri
+    theta, Z = np.linalg.eigh(0.5 * (Hs + Hs.T))
+    return theta, Ri @ Z
+
+
 def bottom_k(g, k):
     """Ground truth by dense symmetric eigendecomposition of D - A (small graphs)."""
     lam, U = np.linalg.eigh(dense_laplacian(g))

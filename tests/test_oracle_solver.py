@@ -165,3 +165,37 @@ def test_edge_gradient_against_finite_differences():
         wm[e] -= hm
         fd = (f(wp) - f(wm)) / (hp + hm)
         assert fd == pytest.approx(grad[e], rel=2e-5, abs=1e-8)
+
+
+def test_rayleigh_ritz_invariant_subspace_gives_exact_eigenpairs():
+    # path graph P_n: lambda_j = 2 - 2 cos(pi j / n), u_j(x) = cos(pi j (x + 1/2) / n)
+    n, k = 40, 5
+    g = gen.path(n)
+    x = np.arange(n) + 0.5
+    U = np.stack([np.cos(np.pi * j * x / n) for j in range(k)], axis=1)
+    lam = 2.0 - 2.0 * np.cos(np.pi * np.arange(k) / n)
+    G = np.random.default_rng(1).standard_normal((k, k))  # any basis of the same span
+    theta, W = oracle.rayleigh_ritz(g, U @ G)
+    assert np.allclose(theta, lam, atol=1e-12)
+    X = U @ G @ W  # Ritz vectors: orthonormal eigenvectors, up to sign
+    assert np.allclose(X.T @ X, np.eye(k), atol=1e-12)
+    for i in range(k):
+        u = U[:, i] / np.linalg.norm(U[:, i])
+        assert abs(abs(u @ X[:, i]) - 1.0) <= 1e-12
+
+
+def test_rayleigh_ritz_interlacing_and_galerkin_condition():
+    # cycle C_n: lambda = 2 - 2 cos(2 pi j / n); for any k-dimensional span the i-th Ritz
+    # value lies between the i-th smallest and the i-th of the top k eigenvalues (Cauchy)
+    n, k = 31, 6
+    g = gen.cycle(n)
+    lam = np.sort(2.0 - 2.0 * np.cos(2.0 * np.pi * np.arange(n) / n))
+    V = np.random.default_rng(2).standard_normal((n, k))
+    theta, W = oracle.rayleigh_ritz(g, V)
+    assert np.all(np.diff(theta) >= -1e-12)
+    assert np.all(theta >= lam[:k] - 1e-12) and np.all(theta <= lam[n - k:] + 1e-12)
+    X = V @ W
+    R = oracle.laplacian_apply(g, X) - X * theta  # residuals orthogonal to span(V)
+    assert np.abs(V.T @ R).max() <= 1e-10 * np.abs(V).max() * np.abs(X).max() * n
+    theta2, _ = oracle.rayleigh_ritz(g, V @ np.random.default_rng(3).standard_normal((k, k)))
+    assert np.allclose(theta2, theta, atol=1e-12)
