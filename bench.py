@@ -48,12 +48,13 @@ def spmm_bytes(n, nnz, k, b_in, b_out, weighted=False):
     return 4 * (n + 1) + 4 * nnz + (4 * nnz if weighted else 0) + n * k * b_in + n * k * b_out
 
 
-def step_bytes(n, nnz, k, ell):
-    """One mixed-precision dilated solver step (F32 master V, BF16 chain, F32 Y)."""
-    chain = spmm_bytes(n, nnz, k, 4, 2) + (ell - 2) * spmm_bytes(n, nnz, k, 2, 2) + \
-        spmm_bytes(n, nnz, k, 2, 4)
+def step_bytes(n, nnz, k, ell, shadow=True):
+    """One mixed-precision dilated solver step (F32 master V, BF16 chain, F32 Y). With the BF16
+    shadow of V the first chain step reads the shadow and the update also writes it."""
+    chain = spmm_bytes(n, nnz, k, 2 if shadow else 4, 2) + \
+        (ell - 2) * spmm_bytes(n, nnz, k, 2, 2) + spmm_bytes(n, nnz, k, 2, 4)
     gram = n * k * 4 * 2
-    update = n * k * 4 * 3
+    update = n * k * 4 * 3 + (n * k * 2 if shadow else 0)
     return chain, chain + gram + update
 
 
@@ -166,6 +167,28 @@ def _principal_angle(sped, Vstar, V, k):
     return float(math.asin(math.sqrt(max(0.0, 1.0 - min(1.0, smin) ** 2))))
 
 
+def _eigen_errors(sped, torch, G, V, k, master, Vref, theta_ref, dense):
+    """Per-eigenpair errors of an arm's result: its Ritz values of L against the reference's
+    (and the dense eigendecomposition's when given), and the angle between each of its Ritz
+    vectors and the matching reference Ritz vector (Vref holds the reference Ritz vectors)."""
+    X = V.clone()
+    theta, _ = sped.rayleigh_ritz(G, X, k, rotate=True)
+    theta = theta.cpu().numpy()
+    C = sped.gram(Vref, k, X.to(torch.float64) if master != torch.float64 else X, k).cpu().numpy()
+    cos = np.clip(np.abs(np.diag(C[:k, k:])) / np.sqrt(np.diag(C[:k, :k]) * np.diag(C[k:, k:])),
+                  0.0, 1.0)
+    out = {"ritz_value_abs_error": [float(x) for x in np.abs(theta - theta_ref)],
+           "ritz_vector_angle": [float(x) for x in np.arccos(cos)]}
+    if dense is not None:
+        lam, U = dense
+        Xh = X[:, :k].double().cpu().numpy()
+        Xh /= np.linalg.norm(Xh, axis=0)
+        out["dense_eigenvalue_abs_error"] = [float(x) for x in np.abs(theta - lam)]
+        out["dense_eigenvector_angle"] = [float(x) for x in
+                                          np.arccos(np.clip(np.abs(np.sum(Xh * U, axis=0)), 0, 1))]
+    return out
+
+
 TTK_ARMS = {
     # name: polynomial, solver, eta (None = 2 / lambda*), chain phases, master dtype, step cap
     "dilated_mixed_mu_eg": dict(poly=("limit", 7), solver="mu_eg", eta=1.5,
@@ -200,9 +223,22 @@ def time_to_bottom_k(sped, torch, g, k, dev, stream, ell_ref, ref_steps=14):
     for _ in range(ref_steps):
         sped.eig_step(G, Vs, k, ref_opts, stats=stats, scratch=scr)
     torch.cuda.synchronize()
+    # reference Ritz pairs of L (rotate the reference block into its Ritz vectors)
+    theta_ref, _ = sped.rayleigh_ritz(G, Vs, k, rotate=True)
+    theta_ref = theta_ref.cpu().numpy()
     out = {"graph": g.name, "n": n, "nnz": g.nnz, "k": k,
            "reference": {"solver": "oja_fp64_limit", "degree": ell_ref, "steps": ref_steps,
-                         "invariant_subspace_residual": float(stats[k:2 * k].max())}}
+                         "invariant_subspace_residual": float(stats[k:2 * k].max()),
+                         "ritz_values": [float(x) for x in theta_ref]}}
+    dense = None
+    if n <= 4000:  # small graph: also against the dense FP64 eigendecomposition of L
+        Ld = np.zeros((n, n))
+        rows = np.repeat(np.arange(n), np.diff(g.row_ptr))
+        Ld[rows, g.col_idx] = -(g.w if g.w is not None else 1.0)
+        Ld[np.arange(n), np.arange(n)] = -Ld.sum(axis=1)
+        lam, U = np.linalg.eigh(Ld)
+        dense = (lam[:k], U[:, :k])
+        out["reference"]["dense_eigenvalue_error_max"] = float(np.abs(theta_ref - lam[:k]).max())
     del scr
     for name, a in TTK_ARMS.items():
         info = (G.set_polynomial(sped.POLY_LIMIT_EXP, a["poly"][1]) if a["poly"][0] == "limit"
@@ -244,6 +280,7 @@ def time_to_bottom_k(sped, torch, g, k, dev, stream, ell_ref, ref_steps=14):
             e1.synchronize()
             rec["ms"] = e0.elapsed_time(e1)
             rec["angle_after_timed_run"] = _principal_angle(sped, Vs, V, k)
+            rec.update(_eigen_errors(sped, torch, G, V, k, master, Vs, theta_ref, dense))
         out[name] = rec
         del scr, V
     p = out["plain_fp64_mu_eg"].get("ms")
@@ -334,7 +371,7 @@ def measure_permuted(sped, torch, dev, stream, k, ell, steps=20):
     for _ in range(3):
         step()
     ms = _timed(torch, stream, step, steps)
-    _, step_b = step_bytes(g.n, g.nnz, k, ell)
+    _, step_b = step_bytes(g.n, g.nnz, k, ell, shadow=False)
     return {"workload": f"sbm_n{g.n}_b{w['blocks']}_deg16_k{k}_permuted", "nnz": g.nnz,
             "ms_per_step": ms, "gbs": step_b / (ms * 1e-3) / 1e9}
 
@@ -519,7 +556,7 @@ def _config(g):
     return {"workload": f"sbm_n{w['n']}_b{w['blocks']}_deg16_k{w['k']}",
             "n": g.n, "nnz": g.nnz, "k": w["k"], "degree_l": w["ell"], "blocks": w["blocks"],
             "p_in": w["p_in"], "p_out": w["p_out"], "seed": SEED,
-            "chain": "bf16 storage, f32 accumulate; f32 master V; f64 k x k",
+            "chain": "bf16 storage, f32 accumulate; f32 master V with a bf16 shadow; f64 k x k",
             "solver": "mu-EG, eta=1.0, limit form (I - sL)^l",
             "l2": "working set (graph 68 MB + blocks >= 200 MB) larger than L2 (129 MB)"}
 
@@ -539,11 +576,14 @@ def run_ours(args, rank, world, local_rank):
     V0 = V0 / V0.norm(dim=0)
     V = sped.alloc_block(g.n, k, torch.float32, dev)
     V[:, :k] = V0.float()
-    opts = sped.step_opts(sped.MU_EG, 1.0, torch.bfloat16, torch.float32)
+    # the update keeps a BF16 shadow of V that the next step's first chain launch reads
+    Vb = sped.alloc_block(g.n, k, torch.bfloat16, dev)
+    opts = sped.step_opts(sped.MU_EG, 1.0, torch.bfloat16, torch.float32, v_shadow=Vb)
     scr = torch.empty(sped.eig_step_scratch_bytes(G, opts, k), dtype=torch.uint8, device=dev)
     K, W = args.steps, args.warmup
     for _ in range(W):
         sped.eig_step(G, V, k, opts, scratch=scr)
+        opts.shadow_valid = 1
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(K)]
     for b, e in ev:  # torch creates the underlying cudaEvent_t at the first record
@@ -596,6 +636,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
+    opts.shadow_valid = 0  # V arrives from the host every step: the chain starts from V
     for _ in range(e2e_steps):
         V.copy_(hostV, non_blocking=True)
         sped.eig_step(G, V, k, opts, scratch=scr)

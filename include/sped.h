@@ -243,6 +243,15 @@ typedef struct {
      * before and after the p(L) V chain, for live timing of the dominant kernel */
     void *ev_chain_begin;
     void *ev_chain_end;
+    /* optional BF16 shadow of the master V (device, n x shadow_ld BF16, shadow_ld * 2 a
+     * multiple of 16 bytes, 16-byte aligned; NULL = none; F32 master only). The update writes
+     * bf16(V_new) into it. When shadow_valid is nonzero the caller asserts that it holds
+     * bf16(V) on entry (as left by the previous step with the same shadow and no change to V
+     * since), and with a BF16 exact chain the first chain launch reads it instead of the F32
+     * master (k-column BF16 rows instead of F32 rows). */
+    void *v_shadow;
+    int shadow_ld;
+    int shadow_valid;
 } sped_step_opts;
 
 sped_status sped_eig_step(const sped_graph *g, const sped_step_opts *opts, void *d_V,
@@ -258,6 +267,19 @@ sped_status sped_rayleigh(const sped_graph *g, const void *d_V, sped_dtype v_t, 
                           double *d_out, void *d_scratch, size_t scratch_bytes, void *stream);
 
 sped_status sped_rayleigh_scratch_size(const sped_graph *g, int k, size_t *bytes);
+
+/* Rayleigh-Ritz: the Ritz pairs of L on span(V) in FP64. With R the upper Cholesky factor of
+ * V^T V, theta and Z are the eigenvalues (ascending) and eigenvectors of the symmetric k x k
+ * matrix R^{-T} (V^T L V) R^{-1} (cyclic Jacobi rotations on one CTA), and W = R^{-1} Z, so the
+ * columns of V W are orthonormal Ritz vectors. d_theta: k doubles; d_W: k x k row-major
+ * doubles (W[j*k + i] = coefficient of v_j in Ritz vector i), may be NULL; rotate != 0
+ * replaces V by V W in place. When V^T V is not positive definite theta is NaN (and V is left
+ * unchanged only if rotate == 0). k <= 32, V F32 or F64. */
+sped_status sped_rayleigh_ritz(const sped_graph *g, void *d_V, sped_dtype v_t, int k, int ld,
+                               double *d_theta, double *d_W, int rotate, void *d_scratch,
+                               size_t scratch_bytes, void *stream);
+
+sped_status sped_rayleigh_ritz_scratch_size(const sped_graph *g, int k, size_t *bytes);
 
 /* ------------------------------------------------------------------------------------
  * Iterate eig_step to convergence (synchronising). The convergence measure is the largest

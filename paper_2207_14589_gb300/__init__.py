@@ -51,7 +51,8 @@ class sped_step_opts(ctypes.Structure):
     _fields_ = [("solver", ctypes.c_int), ("eta", ctypes.c_double), ("chain_t", ctypes.c_int),
                 ("y_t", ctypes.c_int), ("mode", ctypes.c_int), ("walkers", ctypes.c_int64),
                 ("seed", ctypes.c_uint64), ("ev_chain_begin", ctypes.c_void_p),
-                ("ev_chain_end", ctypes.c_void_p)]
+                ("ev_chain_end", ctypes.c_void_p), ("v_shadow", ctypes.c_void_p),
+                ("shadow_ld", ctypes.c_int), ("shadow_valid", ctypes.c_int)]
 
 
 class sped_solve_opts(ctypes.Structure):
@@ -106,6 +107,8 @@ def lib():
         "sped_eig_step_scratch_size": [vp, P(sped_step_opts), i32, P(sz)],
         "sped_rayleigh": [vp, vp, i32, i32, i32, vp, vp, sz, vp],
         "sped_rayleigh_scratch_size": [vp, i32, P(sz)],
+        "sped_rayleigh_ritz": [vp, vp, i32, i32, i32, vp, vp, i32, vp, sz, vp],
+        "sped_rayleigh_ritz_scratch_size": [vp, i32, P(sz)],
         "sped_solve_bottom_k": [vp, P(sped_solve_opts), vp, i32, i32, i32, P(dbl),
                                 P(sped_solve_report), vp, sz, vp],
         "sped_solve_scratch_size": [vp, P(sped_solve_opts), i32, P(sz)],
@@ -334,9 +337,19 @@ def gram(A, ka, B=None, kb=0, G=None, scratch=None, stream=None):
 
 
 def step_opts(solver=MU_EG, eta=1.0, chain_dtype=torch.float32, y_dtype=torch.float32,
-              mode=EXACT, walkers=0, seed=0):
-    return sped_step_opts(solver, float(eta), _TORCH_DT[chain_dtype], _TORCH_DT[y_dtype], mode,
-                          int(walkers), int(seed), None, None)
+              mode=EXACT, walkers=0, seed=0, v_shadow=None, shadow_valid=False):
+    """Options of one solver step. v_shadow: optional BF16 block (alloc_block(n, k, bfloat16))
+    that the update keeps equal to bf16(V); shadow_valid says it already holds bf16(V), so a
+    BF16 chain starts from it."""
+    o = sped_step_opts(solver, float(eta), _TORCH_DT[chain_dtype], _TORCH_DT[y_dtype], mode,
+                       int(walkers), int(seed), None, None, None, 0, 0)
+    if v_shadow is not None:
+        if v_shadow.dtype != torch.bfloat16:
+            raise ValueError("the shadow of V is a bfloat16 block")
+        o.v_shadow = v_shadow.data_ptr()
+        o.shadow_ld = v_shadow.stride(0)
+        o.shadow_valid = int(bool(shadow_valid))
+    return o
 
 
 def eig_step_scratch_bytes(g: Graph, opts: sped_step_opts, k):
@@ -365,6 +378,20 @@ def rayleigh(g: Graph, V, k, out=None, stream=None):
     _check(lib().sped_rayleigh(g.handle, _ptr(V), vt, k, ld, _ptr(out), _ptr(scr), nb.value,
                                _stream(stream)))
     return out
+
+
+def rayleigh_ritz(g: Graph, V, k, rotate=False, stream=None):
+    """Ritz values (ascending, FP64) and coefficients W (V W = Ritz vectors) of L on span(V);
+    rotate=True also replaces V by V W."""
+    vt, ld = _block(V, k)
+    nb = ctypes.c_size_t()
+    _check(lib().sped_rayleigh_ritz_scratch_size(g.handle, k, ctypes.byref(nb)))
+    scr = _scratch(nb.value, V.device)
+    theta = torch.empty(k, dtype=torch.float64, device=V.device)
+    W = torch.empty((k, k), dtype=torch.float64, device=V.device)
+    _check(lib().sped_rayleigh_ritz(g.handle, _ptr(V), vt, k, ld, _ptr(theta), _ptr(W),
+                                    int(bool(rotate)), _ptr(scr), nb.value, _stream(stream)))
+    return theta, W
 
 
 def solve_opts(solver=MU_EG, eta=1.0, chain_dtype=torch.bfloat16, y_dtype=torch.float32,

@@ -232,13 +232,14 @@ __device__ __forceinline__ void load_row(const T *p, int k, bool vec, Acc *out) 
 // V <- (V A + Y B) diag(scale), in place, one row per thread. The coefficient matrices sit in
 // shared memory as [j][i] with i contiguous, so one 16-byte shared load feeds four outputs;
 // B is diagonal for mu-EG (bdiag), which skips its k^2 products. The row is held in registers,
-// so each group of four outputs is stored as soon as it is computed. With STATS it also
-// accumulates, per column, ||v_new_i - v_i||^2 and the invariant-subspace residual
+// so each group of four outputs is stored as soon as it is computed (and, with a shadow, its
+// BF16 rounding into the shadow row, which the next step's BF16 chain starts from). With STATS
+// it also accumulates, per column, ||v_new_i - v_i||^2 and the invariant-subspace residual
 // ||y_i - V C_i||^2 (old V); without, it is the plain update (one read of V and Y, one write).
 template <typename Tm, typename Ty, int KM, bool STATS>
 __global__ void __launch_bounds__(256)
 k_update(int64_t n, Tm *__restrict__ V, int ldv, const Ty *__restrict__ Y, int ldy, int k,
-         Coefs *cf, int bdiag, int vec) {
+         Coefs *cf, int bdiag, int vec, __nv_bfloat16 *__restrict__ shadow, int lds) {
     using A = typename AccOf<Tm>::type;
     static_assert(KM % 4 == 0, "KM");
     __shared__ __align__(16) A sA[KM * KM];
@@ -272,6 +273,7 @@ k_update(int64_t n, Tm *__restrict__ V, int ldv, const Ty *__restrict__ Y, int l
         A v[KM], y[KM];
         load_row<KM, false>(vr, k, vec != 0, v);
         load_row<KM, true>(yr, k, vec != 0, y);
+        uint32_t sw0 = 0, sw1 = 0;  // first half of the shadow chunk being built (8 BF16 values)
 #pragma unroll
         for (int i0 = 0; i0 < KM; i0 += 4) {
             if (i0 >= k) break;
@@ -306,6 +308,31 @@ k_update(int64_t n, Tm *__restrict__ V, int ldv, const Ty *__restrict__ Y, int l
                 }
                 o[q] = from_acc<Tm>(s[q]);
             }
+            if (shadow) {  // BF16 copy of the new row in 16-byte chunks of eight values
+                const __nv_bfloat162 lo2 = __floats2bfloat162_rn((float)o[0], (float)o[1]);
+                const __nv_bfloat162 hi2 = __floats2bfloat162_rn((float)o[2], (float)o[3]);
+                const uint32_t w0 = *reinterpret_cast<const uint32_t *>(&lo2);
+                const uint32_t w1 = *reinterpret_cast<const uint32_t *>(&hi2);
+                __nv_bfloat16 *sr = shadow + r * lds + (i0 & ~7);
+                if ((i0 & 7) == 0) {
+                    sw0 = w0;
+                    sw1 = w1;
+                    if (i0 + 4 >= k) {  // the row ends inside this half chunk
+                        if (i0 + 4 == k) *reinterpret_cast<uint2 *>(sr) = make_uint2(w0, w1);
+                        else
+#pragma unroll
+                            for (int q = 0; q < 3; ++q)
+                                if (i0 + q < k) sr[q] = __float2bfloat16_rn((float)o[q]);
+                    }
+                } else if (i0 + 4 <= k) {
+                    *reinterpret_cast<uint4 *>(sr) = make_uint4(sw0, sw1, w0, w1);
+                } else {
+                    *reinterpret_cast<uint2 *>(sr) = make_uint2(sw0, sw1);
+#pragma unroll
+                    for (int q = 0; q < 3; ++q)
+                        if (i0 + q < k) sr[4 + q] = __float2bfloat16_rn((float)o[q]);
+                }
+            }
             if (vec && i0 + 4 <= k) {
                 if (sizeof(Tm) == 4) {
                     *reinterpret_cast<uint4 *>(vr + i0) = *reinterpret_cast<const uint4 *>(o);
@@ -320,25 +347,26 @@ k_update(int64_t n, Tm *__restrict__ V, int ldv, const Ty *__restrict__ Y, int l
             }
         }
     }
-    if (!STATS) return;
-    // column sums: warp shuffle, then shared, then one atomic per block and column
+    if constexpr (STATS) {
+        // column sums: warp shuffle, then shared, then one atomic per block and column
 #pragma unroll
-    for (int i = 0; i < (STATS ? KM : 1); ++i) {
-        A x = dv[i], z = rs[i];
+        for (int i = 0; i < (STATS ? KM : 1); ++i) {
+            A x = dv[i], z = rs[i];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            x += __shfl_down_sync(0xffffffffu, x, o);
-            z += __shfl_down_sync(0xffffffffu, z, o);
+            for (int o = 16; o > 0; o >>= 1) {
+                x += __shfl_down_sync(0xffffffffu, x, o);
+                z += __shfl_down_sync(0xffffffffu, z, o);
+            }
+            if ((threadIdx.x & 31) == 0 && i < k) {
+                atomicAdd(&sdv[i], (double)x);
+                atomicAdd(&sres[i], (double)z);
+            }
         }
-        if ((threadIdx.x & 31) == 0 && i < k) {
-            atomicAdd(&sdv[i], (double)x);
-            atomicAdd(&sres[i], (double)z);
+        __syncthreads();
+        if (threadIdx.x < k) {
+            atomicAdd(&cf->dv2[threadIdx.x], sdv[threadIdx.x]);
+            atomicAdd(&cf->res2[threadIdx.x], sres[threadIdx.x]);
         }
-    }
-    __syncthreads();
-    if (threadIdx.x < k) {
-        atomicAdd(&cf->dv2[threadIdx.x], sdv[threadIdx.x]);
-        atomicAdd(&cf->res2[threadIdx.x], sres[threadIdx.x]);
     }
 }
 
@@ -356,9 +384,172 @@ __global__ void k_rayleigh_out(const double *G, int k, double *out) {
     if (i < k) out[i] = G[i * 2 * k + k + i] / G[i * 2 * k + i];
 }
 
+// Rayleigh-Ritz on one CTA. G = [V LV]^T [V LV] (2k x 2k): P = V^T V = R^T R (Cholesky),
+// Hs = R^{-T} H R^{-1} with H = V^T L V (the matrix of L in the orthonormal basis V R^{-1}),
+// Hs = Z diag(theta) Z^T by cyclic Jacobi rotations, then W = R^{-1} Z so that V W are the Ritz
+// vectors. Each round applies m/2 disjoint rotations at once (round-robin pairing of the m =
+// k rounded up to even indices; an odd k gets an idle index whose rotations are the identity):
+// the rotation angles from the 2 x 2 blocks, then all row pairs, then all column pairs (and Z).
+// Sweeps stop when the off-diagonal mass is below 1e-30 of the diagonal's, or after RR_SWEEPS.
+constexpr int RR_SWEEPS = 40;
+
+__global__ void __launch_bounds__(SMALL_THREADS)
+k_rayleigh_ritz(const double *__restrict__ G, int k, double *__restrict__ theta,
+                double *__restrict__ W) {
+    __shared__ double sA[MAXK * SLD], sR[MAXK * SLD], sZ[MAXK * SLD], sT[MAXK * SLD], rinv[MAXK];
+    __shared__ double rc[MAXK / 2], rs[MAXK / 2], red[SMALL_THREADS / 32][2];
+    __shared__ int bad, perm[MAXK], done;
+    const int t = threadIdx.x, nt = blockDim.x;
+    const int K2 = 2 * k, m = (k + 1) & ~1;
+    if (t == 0) {
+        bad = 0;
+        done = 0;
+    }
+    for (int e = t; e < MAXK * SLD; e += nt) {
+        sA[e] = 0.0;
+        sZ[e] = 0.0;
+    }
+    __syncthreads();
+    for (int e = t; e < k * k; e += nt) {
+        const int i = e / k, j = e % k;
+        sA[i * SLD + j] = G[i * K2 + j];       // P, consumed by the factorisation
+        sT[i * SLD + j] = G[i * K2 + k + j];   // H
+    }
+    __syncthreads();
+    chol_rl(sA, sR, rinv, k, &bad);
+    if (bad) {
+        for (int i = t; i < k; i += nt) theta[i] = NAN;
+        return;
+    }
+    // Hs = R^{-T} (R^{-T} H)^T, H symmetric
+    trsv_upper_t(sR, rinv, sT, sA, k, k);  // sA = R^{-T} H
+    for (int e = t; e < k * k; e += nt) {
+        const int i = e / k, j = e % k;
+        sT[j * SLD + i] = sA[i * SLD + j];
+    }
+    __syncthreads();
+    trsv_upper_t(sR, rinv, sT, sA, k, k);  // sA = Hs
+    for (int e = t; e < MAXK * SLD; e += nt) sT[e] = 0.0;
+    __syncthreads();
+    for (int e = t; e < k * k; e += nt) {
+        const int i = e / k, j = e % k;
+        if (i <= j) {
+            const double v = 0.5 * (sA[i * SLD + j] + sA[j * SLD + i]);
+            sT[i * SLD + j] = v;
+            sT[j * SLD + i] = v;
+        }
+    }
+    for (int i = t; i < m; i += nt) sZ[i * SLD + i] = 1.0;
+    __syncthreads();
+    // ---- Jacobi sweeps on sT (m x m, the idle index, if any, has zero off-diagonals)
+    const int half = m / 2;
+    for (int sweep = 0; sweep < RR_SWEEPS; ++sweep) {
+        for (int r = 0; r < m - 1; ++r) {
+            // pair i: positions i and m-1-i of the circle [0, (1..m-1 rotated by r)]
+            auto player = [&](int pos) { return pos == 0 ? 0 : 1 + (pos - 1 + r) % (m - 1); };
+            if (t < half) {
+                int p = player(t), q = player(m - 1 - t);
+                if (p > q) {
+                    const int x = p;
+                    p = q;
+                    q = x;
+                }
+                const double apq = sT[p * SLD + q];
+                double c = 1.0, sn = 0.0;
+                if (apq != 0.0) {
+                    const double tau = (sT[q * SLD + q] - sT[p * SLD + p]) / (2.0 * apq);
+                    const double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                    c = rsqrt(1.0 + tt * tt);
+                    sn = tt * c;
+                }
+                rc[t] = c;
+                rs[t] = sn;
+            }
+            __syncthreads();
+            for (int e = t; e < half * m; e += nt) {  // rows p, q <- J^T A
+                const int i = e / m, j = e % m;
+                int p = player(i), q = player(m - 1 - i);
+                if (p > q) {
+                    const int x = p;
+                    p = q;
+                    q = x;
+                }
+                const double c = rc[i], sn = rs[i];
+                const double ap = sT[p * SLD + j], aq = sT[q * SLD + j];
+                sT[p * SLD + j] = c * ap - sn * aq;
+                sT[q * SLD + j] = sn * ap + c * aq;
+            }
+            __syncthreads();
+            for (int e = t; e < half * m; e += nt) {  // columns p, q <- A J, and Z <- Z J
+                const int i = e / m, j = e % m;
+                int p = player(i), q = player(m - 1 - i);
+                if (p > q) {
+                    const int x = p;
+                    p = q;
+                    q = x;
+                }
+                const double c = rc[i], sn = rs[i];
+                const double ap = sT[j * SLD + p], aq = sT[j * SLD + q];
+                sT[j * SLD + p] = c * ap - sn * aq;
+                sT[j * SLD + q] = sn * ap + c * aq;
+                const double zp = sZ[j * SLD + p], zq = sZ[j * SLD + q];
+                sZ[j * SLD + p] = c * zp - sn * zq;
+                sZ[j * SLD + q] = sn * zp + c * zq;
+            }
+            __syncthreads();
+        }
+        // off-diagonal and diagonal mass
+        double off = 0.0, dia = 0.0;
+        for (int e = t; e < m * m; e += nt) {
+            const int i = e / m, j = e % m;
+            const double v = sT[i * SLD + j];
+            if (i == j) dia += v * v;
+            else off += v * v;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            off += __shfl_down_sync(0xffffffffu, off, o);
+            dia += __shfl_down_sync(0xffffffffu, dia, o);
+        }
+        if ((t & 31) == 0) {
+            red[t >> 5][0] = off;
+            red[t >> 5][1] = dia;
+        }
+        __syncthreads();
+        if (t == 0) {
+            double o2 = 0.0, d2 = 0.0;
+            for (int w = 0; w < nt / 32; ++w) {
+                o2 += red[w][0];
+                d2 += red[w][1];
+            }
+            done = !(o2 > 1e-30 * d2);
+        }
+        __syncthreads();
+        if (done) break;
+    }
+    // ---- ascending order (ties by index), W = R^{-1} Z
+    if (t < k) {
+        const double v = sT[t * SLD + t];
+        int rank = 0;
+        for (int j = 0; j < k; ++j) {
+            const double u = sT[j * SLD + j];
+            rank += (u < v || (u == v && j < t)) ? 1 : 0;
+        }
+        perm[rank] = t;
+    }
+    __syncthreads();
+    trsv_upper(sR, rinv, sZ, sA, k, k);  // sA = R^{-1} Z (first k rows and columns of Z)
+    for (int i = t; i < k; i += nt) theta[i] = sT[perm[i] * SLD + perm[i]];
+    if (W)
+        for (int e = t; e < k * k; e += nt) {
+            const int j = e / k, i = e % k;
+            W[j * k + i] = sA[j * SLD + perm[i]];
+        }
+}
+
 template <typename Tm, typename Ty>
 static sped_status run_update(int64_t n, void *V, int ldv, const void *Y, int ldy, int k,
-                              Coefs *cf, int bdiag, bool stats, cudaStream_t st) {
+                              Coefs *cf, int bdiag, bool stats, __nv_bfloat16 *shadow, int lds,
+                              cudaStream_t st) {
     int blocks = device_sm_count() * 4;
     const int64_t need = (n + 255) / 256;
     if (need < blocks) blocks = (int)(need > 0 ? need : 1);
@@ -368,10 +559,10 @@ static sped_status run_update(int64_t n, void *V, int ldv, const void *Y, int ld
     do {                                                                                       \
         if (stats)                                                                             \
             k_update<Tm, Ty, KMV, true><<<blocks, 256, 0, st>>>(n, (Tm *)V, ldv, (const Ty *)Y, \
-                                                                ldy, k, cf, bdiag, vec);       \
+                                                                ldy, k, cf, bdiag, vec, shadow, lds); \
         else                                                                                   \
             k_update<Tm, Ty, KMV, false><<<blocks, 256, 0, st>>>(n, (Tm *)V, ldv, (const Ty *)Y, \
-                                                                 ldy, k, cf, bdiag, vec);      \
+                                                                 ldy, k, cf, bdiag, vec, shadow, lds); \
     } while (0)
     if (k <= 8) UPD(8);
     else if (k <= 16) UPD(16);
@@ -423,6 +614,12 @@ static sped_status check_opts(const sped_step_opts *o) {
     return SPED_OK;
 }
 
+static sped_status check_shadow(const sped_step_opts *o, sped_dtype vt, int k) {
+    if (!o->v_shadow) return SPED_OK;
+    if (vt != SPED_F32) return fail(SPED_ERR_INVALID_ARG, "BF16 shadow needs an F32 master V");
+    return check_layout(o->v_shadow, SPED_BF16, k, o->shadow_ld, "eig_step shadow");
+}
+
 static sped_status eig_step_impl(const sped_graph *g, const sped_step_opts *o, void *V,
                                  sped_dtype vt, int k, int ld, double *d_stats, void *scr_p,
                                  size_t scr_bytes, cudaStream_t st, Coefs **cf_out) {
@@ -435,8 +632,12 @@ static sped_status eig_step_impl(const sped_graph *g, const sped_step_opts *o, v
     Coefs *cf = (Coefs *)(base + L.coefs);
     Scratch shared(base + L.shared, scr_bytes - L.shared);
     if (o->ev_chain_begin) SPED_CUDA(cudaEventRecord((cudaEvent_t)o->ev_chain_begin, st));
+    // a valid BF16 shadow of V feeds the first launch of a BF16 exact chain
+    const bool read_shadow = o->v_shadow && o->shadow_valid && o->chain_t == SPED_BF16 &&
+                             o->mode == SPED_EXACT;
     SPED_TRY(apply_poly_impl(g, k, V, vt, ld, Y, o->y_t, L.ldy, o->chain_t, o->mode, o->walkers,
-                             o->seed, shared, st));
+                             o->seed, shared, st, read_shadow ? o->v_shadow : nullptr, SPED_BF16,
+                             o->shadow_ld));
     if (o->ev_chain_end) SPED_CUDA(cudaEventRecord((cudaEvent_t)o->ev_chain_end, st));
     shared.used = 0;
     SPED_TRY(launch_gram(g->n, V, vt, ld, k, Y, o->y_t, L.ldy, k, G, shared, st));
@@ -444,10 +645,11 @@ static sped_status eig_step_impl(const sped_graph *g, const sped_step_opts *o, v
     k_small<<<1, SMALL_THREADS, 0, st>>>(G, k, o->eta, (int)o->solver, cf, d_stats);
     SPED_CHECK_LAUNCH("k_small");
     const int bdiag = o->solver == SPED_SOLVER_MU_EG;  // mu-EG: Y enters through eta I
-    if (vt == SPED_F32 && o->y_t == SPED_F32) SPED_TRY((run_update<float, float>(g->n, V, ld, Y, L.ldy, k, cf, bdiag, d_stats != nullptr, st)));
-    else if (vt == SPED_F32 && o->y_t == SPED_F64) SPED_TRY((run_update<float, double>(g->n, V, ld, Y, L.ldy, k, cf, bdiag, d_stats != nullptr, st)));
-    else if (vt == SPED_F64 && o->y_t == SPED_F64) SPED_TRY((run_update<double, double>(g->n, V, ld, Y, L.ldy, k, cf, bdiag, d_stats != nullptr, st)));
-    else if (vt == SPED_F64 && o->y_t == SPED_F32) SPED_TRY((run_update<double, float>(g->n, V, ld, Y, L.ldy, k, cf, bdiag, d_stats != nullptr, st)));
+    __nv_bfloat16 *shadow = (__nv_bfloat16 *)o->v_shadow;
+    if (vt == SPED_F32 && o->y_t == SPED_F32) SPED_TRY((run_update<float, float>(g->n, V, ld, Y, L.ldy, k, cf, bdiag, d_stats != nullptr, shadow, o->shadow_ld, st)));
+    else if (vt == SPED_F32 && o->y_t == SPED_F64) SPED_TRY((run_update<float, double>(g->n, V, ld, Y, L.ldy, k, cf, bdiag, d_stats != nullptr, shadow, o->shadow_ld, st)));
+    else if (vt == SPED_F64 && o->y_t == SPED_F64) SPED_TRY((run_update<double, double>(g->n, V, ld, Y, L.ldy, k, cf, bdiag, d_stats != nullptr, nullptr, 0, st)));
+    else if (vt == SPED_F64 && o->y_t == SPED_F32) SPED_TRY((run_update<double, float>(g->n, V, ld, Y, L.ldy, k, cf, bdiag, d_stats != nullptr, nullptr, 0, st)));
     else return fail(SPED_ERR_UNSUPPORTED, "eig_step: master V must be F32 or F64");
     if (d_stats) {
         k_finish_stats<<<1, MAXK, 0, st>>>(k, cf, d_stats);
@@ -486,6 +688,7 @@ sped_status sped_eig_step(const sped_graph *g, const sped_step_opts *opts, void 
     if (v_t != SPED_F32 && v_t != SPED_F64)
         return fail(SPED_ERR_INVALID_ARG, "eig_step: master V must be F32 or F64");
     SPED_TRY(check_layout(d_V, v_t, k, ld, "eig_step V"));
+    SPED_TRY(check_shadow(opts, v_t, k));
     return eig_step_impl(g, opts, d_V, v_t, k, ld, d_stats, d_scratch, scratch_bytes,
                          as_stream(stream), nullptr);
 }
@@ -519,6 +722,45 @@ sped_status sped_rayleigh(const sped_graph *g, const void *d_V, sped_dtype v_t, 
     SPED_TRY(launch_gram(g->n, d_V, v_t, ld, k, LV, SPED_F64, ldl, k, G, scr, st));
     k_rayleigh_out<<<1, 64, 0, st>>>(G, k, d_out);
     SPED_CHECK_LAUNCH("k_rayleigh_out");
+    return SPED_OK;
+}
+
+sped_status sped_rayleigh_ritz_scratch_size(const sped_graph *g, int k, size_t *bytes) {
+    if (!g || !bytes || k < 1 || k > MAXK)
+        return fail(SPED_ERR_INVALID_ARG, "rayleigh_ritz_scratch_size: k in 1..%d", MAXK);
+    size_t b = 0;
+    SPED_TRY(sped_rayleigh_scratch_size(g, k, &b));
+    *bytes = b + align_up(sizeof(double) * k * k, 256) + 256;
+    return SPED_OK;
+}
+
+sped_status sped_rayleigh_ritz(const sped_graph *g, void *d_V, sped_dtype v_t, int k, int ld,
+                               double *d_theta, double *d_W, int rotate, void *d_scratch,
+                               size_t scratch_bytes, void *stream) {
+    if (!g || !d_theta) return fail(SPED_ERR_INVALID_ARG, "rayleigh_ritz: null");
+    if (k < 1 || k > MAXK) return fail(SPED_ERR_UNSUPPORTED, "rayleigh_ritz: k=%d (1..%d)", k, MAXK);
+    if (v_t != SPED_F32 && v_t != SPED_F64)
+        return fail(SPED_ERR_UNSUPPORTED, "rayleigh_ritz: V must be F32 or F64");
+    SPED_TRY(check_layout(d_V, v_t, k, ld, "rayleigh_ritz V"));
+    size_t need = 0;
+    SPED_TRY(sped_rayleigh_ritz_scratch_size(g, k, &need));
+    if (!d_scratch || scratch_bytes < need || ((uintptr_t)d_scratch) % 256)
+        return fail(SPED_ERR_SCRATCH, "rayleigh_ritz: scratch needs %zu bytes", need);
+    cudaStream_t st = as_stream(stream);
+    Scratch scr(d_scratch, scratch_bytes);
+    double *Wk = (double *)scr.take(sizeof(double) * k * k);
+    const int ldl = padded_ld(k, SPED_F64);
+    void *LV = scr.take((size_t)g->n * ldl * 8);
+    double *G = (double *)scr.take(sizeof(double) * 4 * k * k);
+    if (!Wk || !LV || !G) return fail(SPED_ERR_SCRATCH, "rayleigh_ritz: scratch too small");
+    SPED_TRY(launch_poly_step(g, k, d_V, v_t, ld, nullptr, v_t, ld, LV, SPED_F64, ldl, 0.0, 1.0,
+                              0.0, 0, scr, st));
+    SPED_TRY(launch_gram(g->n, d_V, v_t, ld, k, LV, SPED_F64, ldl, k, G, scr, st));
+    k_rayleigh_ritz<<<1, SMALL_THREADS, 0, st>>>(G, k, d_theta, Wk);
+    SPED_CHECK_LAUNCH("k_rayleigh_ritz");
+    if (d_W) SPED_CUDA(cudaMemcpyAsync(d_W, Wk, sizeof(double) * k * k, cudaMemcpyDeviceToDevice, st));
+    if (rotate)  // V <- V W in place: each row is read whole before it is written
+        SPED_TRY(sped_block_combine(g->n, k, d_V, ld, Wk, nullptr, 0, nullptr, d_V, ld, v_t, stream));
     return SPED_OK;
 }
 
@@ -565,6 +807,7 @@ sped_status sped_solve_bottom_k(const sped_graph *g, const sped_solve_opts *opts
     double res = INFINITY;
     for (int step = 1; step <= opts->max_steps; ++step) {
         sped_step_opts so = phase_opts(opts, phase);
+        if (step > 1) so.shadow_valid = 1;  // the previous step left bf16(V) in the shadow
         // the statistics (Rayleigh quotients, residuals, step norms) cost a Cholesky solve and a
         // second k x k product per row, so they are formed on check steps only
         const bool check = step % opts->check_every == 0 || step == opts->max_steps;

@@ -290,9 +290,12 @@ size_t gram_tc_scratch(int64_t n, int ka, int kb);
 sped_status launch_gram_tc(int64_t n, const void *A, sped_dtype at, int lda, int ka, const void *B,
                            sped_dtype bt, int ldb, int kb, double *G, Scratch &scr,
                            cudaStream_t st);
+// X0 (may be NULL): a copy of V in type x0t (leading dimension ldx0) read by the first chain
+// step instead of V
 sped_status apply_poly_impl(const sped_graph *g, int k, const void *V, sped_dtype vt, int ldv,
                             void *Y, sped_dtype yt, int ldy, sped_dtype ct, sped_mode mode,
-                            int64_t walkers, uint64_t seed, Scratch &scr, cudaStream_t st);
+                            int64_t walkers, uint64_t seed, Scratch &scr, cudaStream_t st,
+                            const void *X0, sped_dtype x0t, int ldx0);
 size_t apply_poly_scratch(const sped_graph *g, int k, sped_dtype ct, sped_mode mode);
 sped_status launch_walk(const sped_graph *g, int k, const void *V, sped_dtype vt, int ldv, void *Y,
                         sped_dtype yt, int ldy, sped_mode mode, int64_t walkers, uint64_t seed,

@@ -507,7 +507,8 @@ size_t apply_poly_scratch(const sped_graph *g, int k, sped_dtype ct, sped_mode m
 
 sped_status apply_poly_impl(const sped_graph *g, int k, const void *V, sped_dtype vt, int ldv,
                             void *Y, sped_dtype yt, int ldy, sped_dtype ct, sped_mode mode,
-                            int64_t walkers, uint64_t seed, Scratch &scr, cudaStream_t st) {
+                            int64_t walkers, uint64_t seed, Scratch &scr, cudaStream_t st,
+                            const void *X0, sped_dtype x0t, int ldx0) {
     if (mode != SPED_EXACT)
         return launch_walk(g, k, V, vt, ldv, Y, yt, ldy, mode, walkers, seed, st);
     std::vector<StepCoef> cs = chain_coefs(g->poly);
@@ -523,10 +524,14 @@ sped_status apply_poly_impl(const sped_graph *g, int k, const void *V, sped_dtyp
     const size_t off = align_up(scr.used, 256);
     const size_t rest = (scr.base != nullptr && off < scr.cap) ? scr.cap - off : 0;
     Scratch step_scr(rest ? scr.base + off : nullptr, rest);
+    // the first step reads X0 (a lower-precision copy of V) when the caller provides one
+    const void *x_first = X0 ? X0 : V;
+    const sped_dtype xt_first = X0 ? x0t : vt;
+    const int ldx_first = X0 ? ldx0 : ldv;
     for (int t = 0; t < steps; ++t) {
-        const void *x = t == 0 ? V : b[(t - 1) % 2];
-        sped_dtype xt = t == 0 ? vt : ct;
-        int ldx = t == 0 ? ldv : ldc;
+        const void *x = t == 0 ? x_first : b[(t - 1) % 2];
+        sped_dtype xt = t == 0 ? xt_first : ct;
+        int ldx = t == 0 ? ldx_first : ldc;
         void *y = t == steps - 1 ? Y : b[t % 2];
         sped_dtype ytt = t == steps - 1 ? yt : ct;
         int ldyy = t == steps - 1 ? ldy : ldc;
@@ -587,7 +592,7 @@ sped_status sped_apply_poly(const sped_graph *g, int k, const void *d_V, sped_dt
     if (d_V == d_Y) return fail(SPED_ERR_INVALID_ARG, "apply_poly: V and Y must not alias");
     Scratch scr(d_scratch, scratch_bytes);
     return apply_poly_impl(g, k, d_V, v_t, ldv, d_Y, y_t, ldy, chain_t, mode, walkers, seed, scr,
-                           as_stream(stream));
+                           as_stream(stream), nullptr, SPED_BF16, 0);
 }
 
 }  // extern "C"

@@ -89,6 +89,39 @@ def _sbm_n2000_k4():
     return gen.sbm(2000, 4, 0.05, 0.001, seed=gen.DEFAULT_SEED)
 
 
+def test_bf16_shadow_tracks_master_and_feeds_the_chain():
+    # the update writes bf16(V_new) into the shadow (bit for bit, padding untouched); a step
+    # that starts its BF16 chain from the shadow stays within the BF16 storage bound
+    g = gen.sbm(5000, 5, 0.01, 0.0004, seed=25)
+    G = sped.Graph.from_csr(g)
+    ell = 21
+    info = G.set_polynomial(sped.POLY_LIMIT_EXP, ell)
+    k = 6
+    V0 = gen.gaussian_block(g.n, k, seed=26)
+    V0 /= np.linalg.norm(V0, axis=0)
+    V = to_block(V0, torch.float32)
+    Vb = sped.alloc_block(g.n, k, torch.bfloat16, DEV, fill=float("nan"))
+    opts = sped.step_opts(sped.MU_EG, 1.0, torch.bfloat16, torch.float32, v_shadow=Vb)
+    sped.eig_step(G, V, k, opts)
+    torch.cuda.synchronize()
+    assert torch.equal(Vb[:, :k], V[:, :k].to(torch.bfloat16))
+    if Vb.shape[1] > k:
+        assert torch.isnan(Vb[:, k:]).all()
+    V1 = host(V, k)
+    opts = sped.step_opts(sped.MU_EG, 1.0, torch.bfloat16, torch.float32, v_shadow=Vb,
+                          shadow_valid=True)
+    sped.eig_step(G, V, k, opts)
+    torch.cuda.synchronize()
+    assert torch.equal(Vb[:, :k], V[:, :k].to(torch.bfloat16))
+    want = oracle.mu_eg_step(V1, oracle.poly_limit(g, V1, info.scale_s, ell), 1.0)
+    assert rel(host(V, k), want) <= 1e-2
+    # the shadow needs an F32 master
+    V64 = to_block(V0, torch.float64)
+    with pytest.raises(sped.SpedError):
+        sped.eig_step(G, V64, k, sped.step_opts(sped.MU_EG, 1.0, torch.bfloat16, torch.float64,
+                                                v_shadow=Vb))
+
+
 @pytest.mark.parametrize("arm", ["plain_fp64", "dilated_fp64", "dilated_mixed", "dilated_oja"])
 def test_solve_bottom_k_sbm_n2000_k4(arm):
     g = _sbm_n2000_k4()
@@ -175,3 +208,41 @@ def test_rayleigh_on_closed_form_eigenvectors():
     V = to_block(U, torch.float64)
     lam = sped.rayleigh(G, V, len(js)).cpu().numpy()
     assert np.allclose(lam, [2 - 2 * np.cos(np.pi * j / n) for j in js], rtol=1e-12)
+
+
+@pytest.mark.parametrize("k", [1, 5, 8, 13, 32])
+@pytest.mark.parametrize("vt", [torch.float64, torch.float32])
+def test_rayleigh_ritz_matches_oracle(k, vt):
+    g = gen.sbm(1200, 4, 0.03, 0.002, seed=30 + k)
+    G = sped.Graph.from_csr(g)
+    V0 = gen.gaussian_block(g.n, k, seed=31)
+    V = to_block(V0, vt)
+    theta, W = sped.rayleigh_ritz(G, V, k)
+    Vs = stored(V0, vt)
+    want_t, want_W = oracle.rayleigh_ritz(g, Vs)
+    tol = 1e-10 if vt == torch.float64 else 1e-5
+    assert np.allclose(theta.cpu().numpy(), want_t, rtol=tol, atol=tol * abs(want_t).max())
+    # Ritz vectors agree up to the sign of each column
+    X, Xw = Vs @ W.cpu().numpy(), Vs @ want_W
+    for i in range(k):
+        assert abs(abs(X[:, i] @ Xw[:, i]) - 1.0) <= (1e-8 if vt == torch.float64 else 1e-4)
+    # rotate=True: V becomes the orthonormal Ritz vectors, with the same Ritz values
+    sped.rayleigh_ritz(G, V, k, rotate=True)
+    torch.cuda.synchronize()
+    R = host(V, k)
+    assert np.allclose(R.T @ R, np.eye(k), atol=1e-10 if vt == torch.float64 else 1e-4)
+    theta2, _ = sped.rayleigh_ritz(G, V, k)
+    assert np.allclose(theta2.cpu().numpy(), want_t, rtol=10 * tol, atol=10 * tol * abs(want_t).max())
+
+
+def test_rayleigh_ritz_on_an_invariant_subspace_is_exact():
+    # path graph: the span of the first k closed-form eigenvectors (in a random basis)
+    n, k = 64, 6
+    g = gen.path(n)
+    G = sped.Graph.from_csr(g)
+    x = np.arange(n) + 0.5
+    U = np.stack([np.cos(np.pi * j * x / n) for j in range(k)], axis=1)
+    B = U @ np.random.default_rng(5).standard_normal((k, k))
+    theta, _ = sped.rayleigh_ritz(G, to_block(B, torch.float64), k)
+    assert np.allclose(theta.cpu().numpy(), 2.0 - 2.0 * np.cos(np.pi * np.arange(k) / n),
+                       atol=1e-12)
