@@ -439,11 +439,54 @@ def measure_stochastic(sped, torch, g, G, dev, stream, k, ell, reps=5, err_degre
     return out
 
 
-def measure_batched(sped, torch, dev, stream, k=8, degree=31, steps=4):
+def measure_degree_sweep(sped, torch, dev, stream, k=4, cap=200,
+                         degrees=(11, 51, 151, 251)):
+    """The limit form's degree threshold (cliques graphs of Section 5.4): four 450-cliques joined
+    by 25 short-circuit edges (lambda_max near 450). With the table's scale s = 1/l the factor
+    |1 - s lambda| exceeds 1 on the clique modes for l = 11, 51, 151 and the dilated operator's
+    dominant eigenvectors are no longer the bottom of L; at l = 251 it stays below 1. The
+    automatic scale (s = 2 / lambda_bound when l < lambda_bound / 2) keeps every degree
+    correct. Oja (subspace iteration, eta = 0) in FP64, steps to a largest principal angle
+    <= 1e-3 against the dense eigendecomposition."""
+    g = gen.cliques([450] * 4, short_circuit=25, seed=SEED)
+    n = g.n
+    Ld = np.zeros((n, n))
+    rows = np.repeat(np.arange(n), np.diff(g.row_ptr))
+    Ld[rows, g.col_idx] = -1.0
+    Ld[np.arange(n), np.arange(n)] = -Ld.sum(axis=1)
+    lam, U = np.linalg.eigh(Ld)
+    Ud = sped.alloc_block(n, k, torch.float64, dev)
+    Ud[:, :k] = torch.from_numpy(U[:, :k]).to(dev)
+    G = sped.Graph.from_csr(g, device=dev)
+    V0 = torch.from_numpy(gen.gaussian_block(n, k, seed=SEED + 23)).to(dev)
+    opts = sped.step_opts(sped.OJA, 0.0, torch.float64, torch.float64)
+    out = {"graph": "cliques_4x450_sc25", "n": n, "nnz": g.nnz, "k": k,
+           "lambda_max": float(lam[-1]), "eigengap_k": float(lam[k] - lam[k - 1])}
+    for deg in degrees:
+        for rule, scale in (("table_s_1_over_l", 1.0 / deg), ("automatic_s", 0.0)):
+            info = G.set_polynomial(sped.POLY_LIMIT_EXP, deg, scale=scale)
+            V = sped.alloc_block(n, k, torch.float64, dev)
+            V[:, :k] = V0
+            scr = torch.empty(sped.eig_step_scratch_bytes(G, opts, k), dtype=torch.uint8,
+                              device=dev)
+            steps, ang = None, None
+            for t in range(1, cap + 1):
+                sped.eig_step(G, V, k, opts, scratch=scr)
+                ang = _principal_angle(sped, Ud, V, k)
+                if ang <= 1e-3:
+                    steps = t
+                    break
+            out[f"l{deg}_{rule}"] = {"scale_s": info.scale_s, "converged": steps is not None,
+                                     "steps": steps, "spmm": None if steps is None else steps * deg,
+                                     "final_angle": ang}
+    return out
+
+
+def measure_batched(sped, torch, dev, stream, k=8, degree=31, steps=4, n_graphs=4096):
     """Many independent graphs in one persistent launch (Section 5 applied per graph): 4,096
     SBMs with log-uniform sizes in [200, 20,000], 2-8 blocks, mean degree 12, 87.5 % of edge
     ends inside blocks; k = 8, limit form of degree 31, BF16 chain, mu-EG."""
-    gs = gen.batched_sbm(4096)
+    gs = gen.batched_sbm(n_graphs)
     B = sped.Batch.from_graphs(gs, degree=degree, device=dev)
     n, nnz = B.n_total, int(B.col_idx.numel())
     V = sped.batch_block(n, k, device=dev)
@@ -654,8 +697,9 @@ def run_ours(args, rank, world, local_rank):
         extra["gather_bytes_per_launch"] = g.nnz * k * 2
         extra["stochastic"] = measure_stochastic(sped, torch, g, G, dev, stream, k, ell)
         extra["differentiable"] = measure_differentiable(sped, torch, dev, stream)
-        extra["batched"] = measure_batched(sped, torch, dev, stream)
+        extra["batched"] = measure_batched(sped, torch, dev, stream, n_graphs=args.batched_graphs)
         extra["permuted_node_order"] = measure_permuted(sped, torch, dev, stream, k, ell)
+        extra["degree_sweep"] = measure_degree_sweep(sped, torch, dev, stream)
     if rank == 0 and args.power_law:
         extra["power_law"] = measure_power_law(sped, torch, dev, stream, n=args.power_law_n,
                                                target_nnz=args.target_nnz)
@@ -702,6 +746,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the stochastic, differentiable and batched measurements")
+    ap.add_argument("--batched-graphs", type=int, default=4096,
+                    help="number of graphs of the batched measurement")
     ap.add_argument("--power-law", action="store_true",
                     help="also time the merge-path chain on the 16M-node Chung-Lu graph "
                          "(about 2 minutes of host-side graph generation)")
