@@ -184,6 +184,43 @@ def limit_scalar(lam, s, ell):
     return (1.0 - s * np.asarray(lam, dtype=np.float64)) ** ell
 
 
+def poly_chebyshev(g, V, coeffs, a, b):
+    """sum_j c_j T_j(x) V with x = (2 L - (a + b) I) / (b - a), the Chebyshev polynomials of
+    the first kind by their three-term recurrence (T_0 = 1, T_1 = x, T_{j+1} = 2 x T_j -
+    T_{j-1}); [a, b] is the interval mapped onto [-1, 1]."""
+    V = np.asarray(V, dtype=np.float64)
+    c = np.asarray(coeffs, dtype=np.float64)
+    al, be = 2.0 / (b - a), -(a + b) / (b - a)
+
+    def X(Z):
+        return al * laplacian_apply(g, Z) + be * Z
+    T0 = V
+    Y = c[0] * T0
+    if len(c) > 1:
+        T1 = X(V)
+        Y = Y + c[1] * T1
+        for j in range(1, len(c) - 1):
+            T2 = 2.0 * X(T1) - T0
+            Y = Y + c[j + 1] * T2
+            T0, T1 = T1, T2
+    return Y
+
+
+def chebyshev_scalar(coeffs, x):
+    """sum_j c_j T_j(x) for real x by the closed forms T_j = cos(j arccos x) on [-1, 1] and
+    cosh(j arccosh |x|) (times (-1)^j for x < -1) outside."""
+    x = np.asarray(x, dtype=np.float64)
+    out = np.zeros_like(x)
+    for j, cj in enumerate(coeffs):
+        inside = np.abs(x) <= 1.0
+        t = np.empty_like(x)
+        t[inside] = np.cos(j * np.arccos(x[inside]))
+        ax = np.abs(x[~inside])
+        t[~inside] = np.cosh(j * np.arccosh(ax)) * np.where(x[~inside] < 0, (-1.0) ** j, 1.0)
+        out += cj * t
+    return out
+
+
 def taylor_exp_coeffs(ell):
     """Reversed Taylor -e^{-L} of Table 2 (lambda* = 0, Section 4.2): M = sum_i (-L)^i / i!."""
     return np.array([(-1.0) ** i / math.factorial(i) for i in range(ell + 1)])

@@ -110,3 +110,35 @@ def test_power_coefficients_match_limit():
 def test_scale_rule():
     assert oracle.scale_rule(80.0, 41) == pytest.approx(1 / 41)
     assert oracle.scale_rule(300.0, 41) == pytest.approx(2 / 300)
+
+
+def test_chebyshev_on_closed_form_eigenpairs():
+    # path graph eigenpairs; the interval covers part of the spectrum so both the cos and the
+    # cosh branches of T_j occur
+    n = 30
+    g = gen.path(n)
+    x = np.arange(n) + 0.5
+    j = np.arange(n)
+    U = np.cos(np.pi * np.outer(x, j) / n)
+    lam = 2.0 - 2.0 * np.cos(np.pi * j / n)
+    c = np.array([0.3, -0.7, 0.25, 0.0, 1.1, -0.05, 0.4])
+    a, b = 0.6, 3.2
+    Y = oracle.poly_chebyshev(g, U, c, a, b)
+    want = U * oracle.chebyshev_scalar(c, (2.0 * lam - (a + b)) / (b - a))
+    assert np.allclose(Y, want, rtol=1e-10, atol=1e-9 * np.abs(want).max())
+
+
+def test_chebyshev_product_identity():
+    # T_m T_n = (T_{m+n} + T_{|m-n|}) / 2 as operators on a random block
+    g = gen.random_graph(80, 300, seed=9)
+    V = np.random.default_rng(3).standard_normal((g.n, 3))
+    a, b = 0.0, float(2 * np.diff(g.row_ptr).max())
+    def e(j):
+        c = np.zeros(j + 1)
+        c[j] = 1.0
+        return c
+    for m, k in [(2, 3), (4, 1), (3, 3)]:
+        lhs = oracle.poly_chebyshev(g, oracle.poly_chebyshev(g, V, e(k), a, b), e(m), a, b)
+        rhs = 0.5 * (oracle.poly_chebyshev(g, V, e(m + k), a, b) +
+                     oracle.poly_chebyshev(g, V, e(abs(m - k)), a, b))
+        assert np.allclose(lhs, rhs, rtol=1e-10, atol=1e-10 * np.abs(rhs).max())
