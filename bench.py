@@ -195,6 +195,10 @@ TTK_ARMS = {
                                 chain=("bf16", "f32"), master="f32", cap=400),
     "dilated_mixed_oja": dict(poly=("limit", 15), solver="oja", eta=0.0,
                               chain=("bf16", "f32"), master="f32", cap=200),
+    # Chebyshev filter T_15 on [(theta_k + theta_{k+1}) / 2, lambda_bound] (the reference's
+    # Ritz values): damps the unwanted part of the spectrum, grows fastest below it
+    "chebyshev_filter_mixed_oja": dict(poly=("cheb", 15), solver="oja", eta=0.0,
+                                       chain=("bf16", "f32"), master="f32", cap=200),
     "plain_fp64_mu_eg": dict(poly=("shift", 1), solver="mu_eg", eta=None,
                              chain=("f64",), master="f64", cap=3000),
     "plain_fp32_mu_eg": dict(poly=("shift", 1), solver="mu_eg", eta=None,
@@ -215,20 +219,28 @@ def time_to_bottom_k(sped, torch, g, k, dev, stream, ell_ref, ref_steps=14):
     n = g.n
     V0 = torch.from_numpy(gen.gaussian_block(n, k, seed=SEED)).to(dev)
     G.set_polynomial(sped.POLY_LIMIT_EXP, ell_ref)
-    Vs = sped.alloc_block(n, k, torch.float64, dev)
+    # reference: k + 4 vectors (the extra ones speed it up and estimate lambda_{k+1})
+    kp = k + 4
+    Vs = sped.alloc_block(n, kp, torch.float64, dev)
+    Vs[:, :kp] = torch.from_numpy(gen.gaussian_block(n, kp, seed=SEED + 31)).to(dev)
     Vs[:, :k] = V0
     ref_opts = sped.step_opts(sped.OJA, 0.0, torch.float64, torch.float64)
-    stats = torch.zeros(3 * k, dtype=torch.float64, device=dev)
-    scr = torch.empty(sped.eig_step_scratch_bytes(G, ref_opts, k), dtype=torch.uint8, device=dev)
+    stats = torch.zeros(3 * kp, dtype=torch.float64, device=dev)
+    scr = torch.empty(sped.eig_step_scratch_bytes(G, ref_opts, kp), dtype=torch.uint8, device=dev)
     for _ in range(ref_steps):
-        sped.eig_step(G, Vs, k, ref_opts, stats=stats, scratch=scr)
+        sped.eig_step(G, Vs, kp, ref_opts, stats=stats, scratch=scr)
     torch.cuda.synchronize()
-    # reference Ritz pairs of L (rotate the reference block into its Ritz vectors)
-    theta_ref, _ = sped.rayleigh_ritz(G, Vs, k, rotate=True)
-    theta_ref = theta_ref.cpu().numpy()
+    ref_residual = float(stats[kp:kp + k].max())  # residuals of the first k columns
+    stats = stats[:3 * k]
+    # reference Ritz pairs of L (rotate the reference block into its Ritz vectors, ascending: its
+    # first k columns span the reference bottom-k subspace)
+    theta_all, _ = sped.rayleigh_ritz(G, Vs, kp, rotate=True)
+    theta_all = theta_all.cpu().numpy()
+    theta_ref = theta_all[:k]
     out = {"graph": g.name, "n": n, "nnz": g.nnz, "k": k,
            "reference": {"solver": "oja_fp64_limit", "degree": ell_ref, "steps": ref_steps,
-                         "invariant_subspace_residual": float(stats[k:2 * k].max()),
+                         "vectors": kp, "ritz_value_k_plus_1": float(theta_all[k]),
+                         "invariant_subspace_residual": ref_residual,
                          "ritz_values": [float(x) for x in theta_ref]}}
     dense = None
     if n <= 4000:  # small graph: also against the dense FP64 eigendecomposition of L
@@ -241,8 +253,15 @@ def time_to_bottom_k(sped, torch, g, k, dev, stream, ell_ref, ref_steps=14):
         out["reference"]["dense_eigenvalue_error_max"] = float(np.abs(theta_ref - lam[:k]).max())
     del scr
     for name, a in TTK_ARMS.items():
-        info = (G.set_polynomial(sped.POLY_LIMIT_EXP, a["poly"][1]) if a["poly"][0] == "limit"
-                else G.set_polynomial(sped.POLY_SHIFT, 1))
+        if a["poly"][0] == "limit":
+            info = G.set_polynomial(sped.POLY_LIMIT_EXP, a["poly"][1])
+        elif a["poly"][0] == "cheb":
+            d = a["poly"][1]
+            info = G.set_polynomial(sped.POLY_CHEBYSHEV, d,
+                                    eps=0.5 * float(theta_all[k - 1] + theta_all[k]),
+                                    coeffs=[0.0] * d + [1.0])
+        else:
+            info = G.set_polynomial(sped.POLY_SHIFT, 1)
         eta = a["eta"] if a["eta"] is not None else 2.0 / info.lambda_star
         solver = sped.MU_EG if a["solver"] == "mu_eg" else sped.OJA
         master = dt[a["master"]]
@@ -287,6 +306,8 @@ def time_to_bottom_k(sped, torch, g, k, dev, stream, ell_ref, ref_steps=14):
     best = min([out[a].get("ms") or math.inf for a in ("dilated_mixed_mu_eg", "dilated_mixed_oja")])
     if p and best < math.inf:
         out["speedup_best_dilated_vs_plain_fp64"] = p / best
+    if p and out["chebyshev_filter_mixed_oja"].get("ms"):
+        out["speedup_chebyshev_filter_vs_plain_fp64"] = p / out["chebyshev_filter_mixed_oja"]["ms"]
     if p and out["dilated_mixed_mu_eg"].get("ms"):
         out["speedup_mu_eg_dilated_vs_plain_fp64"] = p / out["dilated_mixed_mu_eg"]["ms"]
     return out
@@ -479,6 +500,55 @@ def measure_degree_sweep(sped, torch, dev, stream, k=4, cap=200,
             out[f"l{deg}_{rule}"] = {"scale_s": info.scale_s, "converged": steps is not None,
                                      "steps": steps, "spmm": None if steps is None else steps * deg,
                                      "final_angle": ang}
+    return out
+
+
+def measure_three_room(sped, torch, dev, stream, k=3, cap_plain=20000, cap_dilated=2000):
+    """Solver steps to the bottom-k (k = 3: one mode per room) subspace of the 3-room grid world
+    of Section 5.3 (s = 2, h = 10: 21 x 61 cells, two walls with one door each), plain reversed
+    Laplacian against the dilated operator of degree 251 (limit form), for subspace iteration
+    (Oja, eta = 0) and mu-EG, FP64; converged at a largest principal angle <= 1e-3 against the
+    dense eigendecomposition."""
+    g = gen.three_room_grid(2, 10)
+    n = g.n
+    Ld = np.zeros((n, n))
+    rows = np.repeat(np.arange(n), np.diff(g.row_ptr))
+    Ld[rows, g.col_idx] = -1.0
+    Ld[np.arange(n), np.arange(n)] = -Ld.sum(axis=1)
+    lam, U = np.linalg.eigh(Ld)
+    Ud = sped.alloc_block(n, k, torch.float64, dev)
+    Ud[:, :k] = torch.from_numpy(U[:, :k]).to(dev)
+    G = sped.Graph.from_csr(g, device=dev)
+    V0 = torch.from_numpy(gen.gaussian_block(n, k, seed=SEED + 29)).to(dev)
+    out = {"graph": g.name, "n": n, "k": k, "lambda_k": float(lam[k - 1]),
+           "lambda_k_plus_1": float(lam[k])}
+    arms = {"plain_oja": ("shift", sped.OJA, 0.0, cap_plain),
+            "dilated251_oja": ("limit", sped.OJA, 0.0, cap_dilated),
+            "plain_mu_eg": ("shift", sped.MU_EG, None, cap_plain),
+            "dilated251_mu_eg": ("limit", sped.MU_EG, 1.0, cap_dilated)}
+    for name, (poly, solver, eta, cap) in arms.items():
+        info = (G.set_polynomial(sped.POLY_LIMIT_EXP, 251) if poly == "limit"
+                else G.set_polynomial(sped.POLY_SHIFT, 1))
+        e = eta if eta is not None else 2.0 / info.lambda_star
+        opts = sped.step_opts(solver, e, torch.float64, torch.float64)
+        V = sped.alloc_block(n, k, torch.float64, dev)
+        V[:, :k] = V0
+        scr = torch.empty(sped.eig_step_scratch_bytes(G, opts, k), dtype=torch.uint8, device=dev)
+        every = 1 if cap <= cap_dilated else 10
+        steps, ang = None, None
+        for t in range(1, cap + 1):
+            sped.eig_step(G, V, k, opts, scratch=scr)
+            if t % every == 0 or t == cap:
+                ang = _principal_angle(sped, Ud, V, k)
+                if ang <= 1e-3:
+                    steps = t
+                    break
+        out[name] = {"steps": steps, "spmm": None if steps is None else steps * info.degree,
+                     "final_angle": ang, "eta": e}
+    for sv in ("oja", "mu_eg"):
+        p_, d_ = out[f"plain_{sv}"]["steps"], out[f"dilated251_{sv}"]["steps"]
+        if p_ and d_:
+            out[f"step_ratio_{sv}"] = p_ / d_
     return out
 
 
@@ -700,6 +770,7 @@ def run_ours(args, rank, world, local_rank):
         extra["batched"] = measure_batched(sped, torch, dev, stream, n_graphs=args.batched_graphs)
         extra["permuted_node_order"] = measure_permuted(sped, torch, dev, stream, k, ell)
         extra["degree_sweep"] = measure_degree_sweep(sped, torch, dev, stream)
+        extra["three_room"] = measure_three_room(sped, torch, dev, stream)
     if rank == 0 and args.power_law:
         extra["power_law"] = measure_power_law(sped, torch, dev, stream, n=args.power_law_n,
                                                target_nnz=args.target_nnz)

@@ -57,7 +57,9 @@ typedef enum {
     SPED_POLY_TAYLOR_EXP = 1, /* M = sum_{i<=l} (-L)^i / i!: reversed Taylor -e^{-L}        */
     SPED_POLY_TAYLOR_LOG = 2, /* M = lambda* I - sum_{i=1}^{l} (-1)^{i+1} (L+(eps-1)I)^i / i */
     SPED_POLY_MONOMIAL = 3,   /* M = sum_i c_i L^i with caller coefficients c_0..c_l        */
-    SPED_POLY_SHIFT = 4       /* M = lambda* I - L: the plain reversed Laplacian, Eq. reveig */
+    SPED_POLY_SHIFT = 4,      /* M = lambda* I - L: the plain reversed Laplacian, Eq. reveig */
+    SPED_POLY_CHEBYSHEV = 5   /* M = sum_i c_i T_i(x), x = (2L - (a+b) I) / (b - a): Chebyshev
+                                 series (or filter) on [a, b], caller coefficients c_0..c_l  */
 } sped_poly_kind;
 
 typedef enum {
@@ -121,6 +123,11 @@ sped_status sped_set_edge_weights(sped_graph *g, const float *d_w_edge, void *st
  *  coeffs     SPED_POLY_MONOMIAL only: l+1 host doubles c_0..c_l.
  *  lambda_star SHIFT and TAYLOR_LOG: 0 = automatic (the spectral bound, or for the log the
  *             series' value bound).
+ *  CHEBYSHEV  coeffs: l+1 host doubles c_0..c_l; eps = a and lambda_star = b (0 = the spectral
+ *             bound) are the ends of the interval mapped onto [-1, 1], a < b. Evaluated by
+ *             Clenshaw's recurrence: l chain steps, each Y = alpha V + gamma X + beta L X -
+ *             (the output of the step before last), three chain buffers. A single c_l = 1 is
+ *             the Chebyshev filter T_l, which damps [a, b] and grows fastest below a.
  * ------------------------------------------------------------------------------------ */
 sped_status sped_set_polynomial(sped_graph *g, sped_poly_kind kind, int degree, double scale_s,
                                 double eps, const double *coeffs, double lambda_star);

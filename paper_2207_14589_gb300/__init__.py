@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libsped.so")
 OK, ERR_INVALID_ARG, ERR_BAD_CSR, ERR_UNSUPPORTED, ERR_NUMERIC, ERR_NOT_CONVERGED, \
     ERR_TIMEOUT, ERR_CUDA, ERR_SCRATCH = range(9)
 BF16, F32, F64 = 0, 1, 2
-POLY_LIMIT_EXP, POLY_TAYLOR_EXP, POLY_TAYLOR_LOG, POLY_MONOMIAL, POLY_SHIFT = range(5)
+POLY_LIMIT_EXP, POLY_TAYLOR_EXP, POLY_TAYLOR_LOG, POLY_MONOMIAL, POLY_SHIFT, POLY_CHEBYSHEV = range(6)
 EXACT, STOCHASTIC_IS, STOCHASTIC_REJECT = range(3)
 MU_EG, OJA = 0, 1
 

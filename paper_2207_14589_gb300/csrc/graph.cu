@@ -340,6 +340,26 @@ static void resolve_power(Poly &P) {
         P.power[1] = -1.0;
         return;
     }
+    if (P.kind == SPED_POLY_CHEBYSHEV) {
+        // T_j(al L + be) in powers of L by the three-term recurrence, summed with c_j
+        const double al = 2.0 / (P.cheb_b - P.cheb_a), be = -(P.cheb_a + P.cheb_b) / (P.cheb_b - P.cheb_a);
+        std::vector<double> t0(P.ell + 1, 0.0), t1(P.ell + 1, 0.0), t2(P.ell + 1, 0.0);
+        t0[0] = 1.0;
+        for (int i = 0; i <= P.ell; ++i) P.power[i] += P.cheb[0] * t0[i];
+        if (P.ell >= 1) {
+            t1[0] = be;
+            t1[1] = al;
+            for (int i = 0; i <= P.ell; ++i) P.power[i] += P.cheb[1] * t1[i];
+        }
+        for (int j = 1; j < P.ell; ++j) {
+            for (int i = 0; i <= P.ell; ++i)
+                t2[i] = 2.0 * (be * t1[i] + (i > 0 ? al * t1[i - 1] : 0.0)) - t0[i];
+            for (int i = 0; i <= P.ell; ++i) P.power[i] += P.cheb[j + 1] * t2[i];
+            t0.swap(t1);
+            t1.swap(t2);
+        }
+        return;
+    }
     for (int i = 0; i <= P.ell; ++i) {
         double c = 0.0;
         for (int j = i; j <= P.ell; ++j)
@@ -559,6 +579,18 @@ sped_status sped_set_polynomial(sped_graph *g, sped_poly_kind kind, int degree, 
         double ls = lambda_star != 0.0 ? lambda_star : g->lambda_bound;
         P.lambda_star = ls;
         P.horner = {ls, -1.0};
+        break;
+    }
+    case SPED_POLY_CHEBYSHEV: {
+        if (!coeffs) return fail(SPED_ERR_INVALID_ARG, "chebyshev: coeffs is NULL");
+        P.cheb.assign(coeffs, coeffs + degree + 1);
+        for (double c : P.cheb)
+            if (!std::isfinite(c)) return fail(SPED_ERR_INVALID_ARG, "chebyshev: non-finite c");
+        P.cheb_a = eps;
+        P.cheb_b = lambda_star != 0.0 ? lambda_star : g->lambda_bound;
+        if (!(P.cheb_b > P.cheb_a) || !std::isfinite(P.cheb_a) || !std::isfinite(P.cheb_b))
+            return fail(SPED_ERR_INVALID_ARG, "chebyshev: interval [%g, %g] is empty", P.cheb_a,
+                        P.cheb_b);
         break;
     }
     default:

@@ -90,6 +90,8 @@ struct Poly {
     double eps = 0.0;
     std::vector<double> horner;  // c_0..c_l in powers of T (Horner kinds)
     std::vector<double> power;   // c_0..c_l in powers of L (stochastic mode)
+    std::vector<double> cheb;    // c_0..c_l of the Chebyshev series (CHEBYSHEV)
+    double cheb_a = 0.0, cheb_b = 0.0;  // interval mapped onto [-1, 1]
 };
 
 }  // namespace sped
@@ -280,6 +282,12 @@ sped_status launch_poly_step(const sped_graph *g, int k, const void *X, sped_dty
                              const void *V, sped_dtype vt, int ldv, void *Y, sped_dtype yt, int ldy,
                              double alpha, double beta, double gamma, int split, Scratch &scr,
                              cudaStream_t st);
+// the same step plus delta * W2 (a block of X's type and layout ldw2; needs V)
+sped_status launch_poly_step_w2(const sped_graph *g, int k, const void *X, sped_dtype xt,
+                                int ldx, const void *V, sped_dtype vt, int ldv, void *Y,
+                                sped_dtype yt, int ldy, double alpha, double beta, double gamma,
+                                const void *W2, int ldw2, double delta, int split, Scratch &scr,
+                                cudaStream_t st);
 size_t poly_step_scratch(const sped_graph *g, int k, sped_dtype xt, int split);
 size_t merge_step_scratch(const sped_graph *g, int k, sped_dtype xt, int ipg);
 sped_status launch_gram(int64_t n, const void *A, sped_dtype at, int lda, int ka, const void *B,

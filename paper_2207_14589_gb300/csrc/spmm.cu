@@ -18,7 +18,7 @@ namespace sped {
 constexpr int STEP_THREADS = 256;
 constexpr int UNROLL = 4;
 
-template <typename Tx, typename Tv, typename Ty, typename A, bool W, bool HV>
+template <typename Tx, typename Tv, typename Ty, typename A, bool W, int HV>
 struct StepArgs {
     int n;
     const int32_t *__restrict__ rp;
@@ -33,10 +33,14 @@ struct StepArgs {
     int k;
     int C;
     A alpha, beta, gamma;
+    const Tx *__restrict__ W2;  // HV == 2: a second block added with weight delta
+    int ldw2;
+    A delta;
 };
 
 // epilogue of row r for the lane's chunk: out = alpha v + gamma x + beta (d x - acc)
-template <typename Tx, typename Tv, typename Ty, typename A, bool W, bool HV, int E>
+// (+ delta w2 when HV == 2: the three-term recurrences)
+template <typename Tx, typename Tv, typename Ty, typename A, bool W, int HV, int E>
 __device__ __forceinline__ void finish_row(const StepArgs<Tx, Tv, Ty, A, W, HV> &a, int64_t r,
                                            int c, const A (&acc)[E], A dsum) {
     A xr[E];
@@ -52,12 +56,19 @@ __device__ __forceinline__ void finish_row(const StepArgs<Tx, Tv, Ty, A, W, HV> 
 #pragma unroll
         for (int i = 0; i < E; ++i) out[i] += a.alpha * vr[i];
     }
+    if constexpr (HV == 2) {
+        A wr[E];
+        if (rem >= E) load_chunk<Tx, E, A>(a.W2 + r * a.ldw2 + c * E, wr);
+        else load_partial<Tx, E, A>(a.W2 + r * a.ldw2 + c * E, rem, wr);
+#pragma unroll
+        for (int i = 0; i < E; ++i) out[i] += a.delta * wr[i];
+    }
     if (rem >= E) store_chunk<Ty, E, A>(a.Y + r * a.ldy + c * E, out);
     else store_partial<Ty, E, A>(a.Y + r * a.ldy + c * E, rem, out);
 }
 
 // accumulate neighbours [p, p1) of the lane's chunk into acc / dsum
-template <typename Tx, typename Tv, typename Ty, typename A, bool W, bool HV, int E>
+template <typename Tx, typename Tv, typename Ty, typename A, bool W, int HV, int E>
 __device__ __forceinline__ void gather_range(const StepArgs<Tx, Tv, Ty, A, W, HV> &a, int c, int p,
                                              int p1, A (&acc)[E], A &dsum) {
     const Tx *Xc = a.X + c * E;
@@ -107,7 +118,7 @@ __device__ __forceinline__ void gather_range(const StepArgs<Tx, Tv, Ty, A, W, HV
 // row share their sectors in L1). 32 registers keep all 64 warps of an SM resident: the kernel
 // is bound by the latency and sector throughput of the random row gathers, so occupancy is
 // what keeps bytes in flight.
-template <typename Tx, typename Tv, typename Ty, typename A, bool W, bool HV>
+template <typename Tx, typename Tv, typename Ty, typename A, bool W, int HV>
 __global__ void __launch_bounds__(STEP_THREADS)
 k_step_rowgroup(StepArgs<Tx, Tv, Ty, A, W, HV> a, int rows_per_warp) {
     constexpr int E = 16 / (int)sizeof(Tx);
@@ -166,7 +177,7 @@ template <typename A> struct MergeParts {
     int KP;
 };
 
-template <typename Tx, typename Tv, typename Ty, typename A, bool W, bool HV>
+template <typename Tx, typename Tv, typename Ty, typename A, bool W, int HV>
 __global__ void __launch_bounds__(STEP_THREADS)
 k_step_merge(StepArgs<Tx, Tv, Ty, A, W, HV> a, int nnz, int groups_per_warp,
              int64_t n_groups, MergeParts<A> parts) {
@@ -272,7 +283,7 @@ k_step_merge(StepArgs<Tx, Tv, Ty, A, W, HV> a, int nnz, int groups_per_warp,
 
 // Finish rows cut by share boundaries: the share holding a row's end sums its head piece and
 // the tail pieces of the preceding shares (walking back while they belong to the row).
-template <typename Tx, typename Tv, typename Ty, typename A, bool W, bool HV>
+template <typename Tx, typename Tv, typename Ty, typename A, bool W, int HV>
 __global__ void __launch_bounds__(STEP_THREADS)
 k_merge_fixup(StepArgs<Tx, Tv, Ty, A, W, HV> a, int groups_per_warp, int64_t n_groups,
               MergeParts<A> parts) {
@@ -337,8 +348,6 @@ static MergePlan merge_plan(const sped_graph *g, int k, sped_dtype xt, size_t ac
     return m;
 }
 
-static size_t acc_size_for(sped_dtype yt) { return yt == SPED_F64 ? 8 : 4; }
-
 size_t merge_step_scratch(const sped_graph *g, int k, sped_dtype xt, int ipg) {
     sped_graph probe_shape;  // only n, nnz and the share size enter the plan
     probe_shape.n = g->n;
@@ -364,10 +373,11 @@ size_t poly_step_scratch(const sped_graph *g, int k, sped_dtype xt, int split) {
     return p.total();
 }
 
-template <typename Tx, typename Tv, typename Ty, typename A, bool W, bool HV>
+template <typename Tx, typename Tv, typename Ty, typename A, bool W, int HV>
 static sped_status run_step(const sped_graph *g, int k, const void *X, int ldx, const void *V,
                             int ldv, void *Y, int ldy, double alpha, double beta, double gamma,
-                            int split, Scratch &scr, cudaStream_t st) {
+                            const void *W2, int ldw2, double delta, int split, Scratch &scr,
+                            cudaStream_t st) {
     constexpr int E = 16 / (int)sizeof(Tx);
     StepArgs<Tx, Tv, Ty, A, W, HV> a;
     a.n = (int)g->n;
@@ -385,6 +395,9 @@ static sped_status run_step(const sped_graph *g, int k, const void *X, int ldx, 
     a.alpha = (A)alpha;
     a.beta = (A)beta;
     a.gamma = (A)gamma;
+    a.W2 = (const Tx *)W2;
+    a.ldw2 = ldw2;
+    a.delta = (A)delta;
     if (a.C > 32) return fail(SPED_ERR_UNSUPPORTED, "poly_step: row of %d chunks > 32", a.C);
     const int per_warp = 32 / a.C;
     if (!use_merge(g, split)) {
@@ -422,47 +435,65 @@ static sped_status run_step(const sped_graph *g, int k, const void *X, int ldx, 
     return SPED_OK;
 }
 
-template <typename Tx, typename Tv, typename Ty, typename A, bool HV>
+template <typename Tx, typename Tv, typename Ty, typename A, int HV>
 static sped_status run_step_w(const sped_graph *g, int k, const void *X, int ldx, const void *V,
-                              int ldv, void *Y, int ldy, double al, double be, double ga, int split,
-                              Scratch &scr, cudaStream_t st) {
+                              int ldv, void *Y, int ldy, double al, double be, double ga,
+                              const void *W2, int ldw2, double de, int split, Scratch &scr,
+                              cudaStream_t st) {
     if (g->w)
-        return run_step<Tx, Tv, Ty, A, true, HV>(g, k, X, ldx, V, ldv, Y, ldy, al, be, ga, split,
-                                                 scr, st);
-    return run_step<Tx, Tv, Ty, A, false, HV>(g, k, X, ldx, V, ldv, Y, ldy, al, be, ga, split,
-                                              scr, st);
+        return run_step<Tx, Tv, Ty, A, true, HV>(g, k, X, ldx, V, ldv, Y, ldy, al, be, ga, W2,
+                                                 ldw2, de, split, scr, st);
+    return run_step<Tx, Tv, Ty, A, false, HV>(g, k, X, ldx, V, ldv, Y, ldy, al, be, ga, W2, ldw2,
+                                              de, split, scr, st);
 }
 
 using bf16 = __nv_bfloat16;
+
+sped_status launch_poly_step_w2(const sped_graph *g, int k, const void *X, sped_dtype xt,
+                                int ldx, const void *V, sped_dtype vt, int ldv, void *Y,
+                                sped_dtype yt, int ldy, double al, double be, double ga,
+                                const void *W2, int ldw2, double de, int split, Scratch &scr,
+                                cudaStream_t st) {
+    const bool hw = W2 != nullptr && de != 0.0;
+    const bool hv = hw || (V != nullptr && al != 0.0);
+    if (hw && !V) return fail(SPED_ERR_INVALID_ARG, "poly_step: a second block needs V");
+#define STEP(TX, TV, TY, ACC, HVV)                                                            \
+    return run_step_w<TX, TV, TY, ACC, HVV>(g, k, X, ldx, V, ldv, Y, ldy, al, be, ga, W2,      \
+                                            ldw2, de, split, scr, st)
+#define STEP_V(TX, TV, TY, ACC)                                                                \
+    do {                                                                                       \
+        if (hw) STEP(TX, TV, TY, ACC, 2);                                                      \
+        STEP(TX, TV, TY, ACC, 1);                                                              \
+    } while (0)
+    if (!hv) {
+        if (xt == SPED_F64 && yt == SPED_F64) STEP(double, double, double, double, 0);
+        if (xt == SPED_F32 && yt == SPED_F32) STEP(float, float, float, float, 0);
+        if (xt == SPED_BF16 && yt == SPED_BF16) STEP(bf16, bf16, bf16, float, 0);
+        if (xt == SPED_F32 && yt == SPED_BF16) STEP(float, float, bf16, float, 0);
+        if (xt == SPED_BF16 && yt == SPED_F32) STEP(bf16, bf16, float, float, 0);
+        if (xt == SPED_F32 && yt == SPED_F64) STEP(float, float, double, double, 0);
+    } else {
+        if (xt == SPED_F64 && yt == SPED_F64 && vt == SPED_F64) STEP_V(double, double, double, double);
+        if (xt == SPED_F64 && yt == SPED_F64 && vt == SPED_F32) STEP_V(double, float, double, double);
+        if (xt == SPED_F32 && yt == SPED_F32 && vt == SPED_F32) STEP_V(float, float, float, float);
+        if (xt == SPED_BF16 && yt == SPED_BF16 && vt == SPED_F32) STEP_V(bf16, float, bf16, float);
+        if (xt == SPED_F32 && yt == SPED_BF16 && vt == SPED_F32) STEP_V(float, float, bf16, float);
+        if (xt == SPED_BF16 && yt == SPED_F32 && vt == SPED_F32) STEP_V(bf16, float, float, float);
+        if (xt == SPED_F32 && yt == SPED_F64 && vt == SPED_F32) STEP_V(float, float, double, double);
+        if (xt == SPED_F32 && yt == SPED_F64 && vt == SPED_F64) STEP_V(float, double, double, double);
+    }
+#undef STEP_V
+#undef STEP
+    return fail(SPED_ERR_UNSUPPORTED, "poly_step: unsupported dtype combination x=%d y=%d v=%d",
+                (int)xt, (int)yt, hv ? (int)vt : -1);
+}
 
 sped_status launch_poly_step(const sped_graph *g, int k, const void *X, sped_dtype xt, int ldx,
                              const void *V, sped_dtype vt, int ldv, void *Y, sped_dtype yt,
                              int ldy, double al, double be, double ga, int split, Scratch &scr,
                              cudaStream_t st) {
-    const bool hv = V != nullptr && al != 0.0;
-#define STEP(TX, TV, TY, ACC, HVV)                                                            \
-    return run_step_w<TX, TV, TY, ACC, HVV>(g, k, X, ldx, V, ldv, Y, ldy, al, be, ga, split,   \
-                                            scr, st)
-    if (!hv) {
-        if (xt == SPED_F64 && yt == SPED_F64) STEP(double, double, double, double, false);
-        if (xt == SPED_F32 && yt == SPED_F32) STEP(float, float, float, float, false);
-        if (xt == SPED_BF16 && yt == SPED_BF16) STEP(bf16, bf16, bf16, float, false);
-        if (xt == SPED_F32 && yt == SPED_BF16) STEP(float, float, bf16, float, false);
-        if (xt == SPED_BF16 && yt == SPED_F32) STEP(bf16, bf16, float, float, false);
-        if (xt == SPED_F32 && yt == SPED_F64) STEP(float, float, double, double, false);
-    } else {
-        if (xt == SPED_F64 && yt == SPED_F64 && vt == SPED_F64) STEP(double, double, double, double, true);
-        if (xt == SPED_F64 && yt == SPED_F64 && vt == SPED_F32) STEP(double, float, double, double, true);
-        if (xt == SPED_F32 && yt == SPED_F32 && vt == SPED_F32) STEP(float, float, float, float, true);
-        if (xt == SPED_BF16 && yt == SPED_BF16 && vt == SPED_F32) STEP(bf16, float, bf16, float, true);
-        if (xt == SPED_F32 && yt == SPED_BF16 && vt == SPED_F32) STEP(float, float, bf16, float, true);
-        if (xt == SPED_BF16 && yt == SPED_F32 && vt == SPED_F32) STEP(bf16, float, float, float, true);
-        if (xt == SPED_F32 && yt == SPED_F64 && vt == SPED_F32) STEP(float, float, double, double, true);
-        if (xt == SPED_F32 && yt == SPED_F64 && vt == SPED_F64) STEP(float, double, double, double, true);
-    }
-#undef STEP
-    return fail(SPED_ERR_UNSUPPORTED, "poly_step: unsupported dtype combination x=%d y=%d v=%d",
-                (int)xt, (int)yt, hv ? (int)vt : -1);
+    return launch_poly_step_w2(g, k, X, xt, ldx, V, vt, ldv, Y, yt, ldy, al, be, ga, nullptr, 0,
+                               0.0, split, scr, st);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -471,6 +502,8 @@ sped_status launch_poly_step(const sped_graph *g, int k, const void *X, sped_dty
 struct StepCoef {
     double alpha, beta, gamma;
     bool uses_v;
+    double delta = 0.0;   // weight of the output of the step before last (Clenshaw)
+    bool uses_w2 = false;
 };
 
 static std::vector<StepCoef> chain_coefs(const Poly &P) {
@@ -479,6 +512,23 @@ static std::vector<StepCoef> chain_coefs(const Poly &P) {
         for (int t = 0; t < P.ell; ++t) out.push_back({0.0, -P.s, 1.0, false});
     } else if (P.kind == SPED_POLY_SHIFT) {
         out.push_back({0.0, -1.0, P.lambda_star, false});
+    } else if (P.kind == SPED_POLY_CHEBYSHEV) {
+        // Clenshaw with x = al L + be I: b_j = c_j V + 2 x b_{j+1} - b_{j+2} (b_{l+1} = b_{l+2}
+        // = 0, so b_l = c_l V is folded into the first two steps), then M V = c_0 V + x b_1 - b_2
+        const auto &c = P.cheb;
+        const int l = P.ell;
+        const double al = 2.0 / (P.cheb_b - P.cheb_a), be = -(P.cheb_a + P.cheb_b) / (P.cheb_b - P.cheb_a);
+        if (l == 1) {
+            out.push_back({0.0, al * c[1], c[0] + be * c[1], false});
+            return out;
+        }
+        out.push_back({0.0, 2.0 * al * c[l], c[l - 1] + 2.0 * be * c[l], false});  // b_{l-1}
+        for (int j = l - 2; j >= 1; --j) {                                        // b_j
+            if (j + 2 == l) out.push_back({c[j] - c[l], 2.0 * al, 2.0 * be, true});
+            else out.push_back({c[j], 2.0 * al, 2.0 * be, true, -1.0, true});
+        }
+        if (l == 2) out.push_back({c[0] - c[2], al, be, true});                 // M V
+        else out.push_back({c[0], al, be, true, -1.0, true});
     } else {
         const auto &h = P.horner;
         const int l = P.ell;
@@ -489,13 +539,20 @@ static std::vector<StepCoef> chain_coefs(const Poly &P) {
     return out;
 }
 
+// chain buffers: two in turn, three when a step also reads the output of the step before last
+static int chain_buffers(const std::vector<StepCoef> &cs) {
+    const int steps = (int)cs.size();
+    bool w2 = false;
+    for (const auto &c : cs) w2 = w2 || c.uses_w2;
+    return steps < 2 ? 0 : steps == 2 ? 1 : (w2 ? 3 : 2);
+}
+
 size_t apply_poly_scratch(const sped_graph *g, int k, sped_dtype ct, sped_mode mode) {
     if (mode != SPED_EXACT) return 0;
-    int steps = (int)chain_coefs(g->poly).size();
+    const int nbuf = chain_buffers(chain_coefs(g->poly));
     ScratchPlan p;
     size_t buf = (size_t)g->n * padded_ld(k, ct) * dtype_size(ct);
-    if (steps >= 2) p.add(buf);
-    if (steps >= 3) p.add(buf);
+    for (int i = 0; i < nbuf; ++i) p.add(buf);
     size_t ms = 0;
     for (sped_dtype t : {SPED_BF16, SPED_F32, SPED_F64}) {
         size_t x = poly_step_scratch(g, k, t, 0);
@@ -515,11 +572,13 @@ sped_status apply_poly_impl(const sped_graph *g, int k, const void *V, sped_dtyp
     const int steps = (int)cs.size();
     const int ldc = padded_ld(k, ct);
     const size_t buf = (size_t)g->n * ldc * dtype_size(ct);
-    void *b[2] = {nullptr, nullptr};
-    if (steps >= 2) b[0] = scr.take(buf);
-    if (steps >= 3) b[1] = scr.take(buf);
-    if ((steps >= 2 && !b[0]) || (steps >= 3 && !b[1]))
-        return fail(SPED_ERR_SCRATCH, "apply_poly: scratch too small for the chain buffers");
+    const int nbuf = chain_buffers(cs);
+    void *b[3] = {nullptr, nullptr, nullptr};
+    for (int i = 0; i < nbuf; ++i) {
+        b[i] = scr.take(buf);
+        if (!b[i]) return fail(SPED_ERR_SCRATCH, "apply_poly: scratch too small for the chain buffers");
+    }
+    const int nb = nbuf > 0 ? nbuf : 1;
     // what is left of the caller's scratch after the chain buffers serves each step in turn
     const size_t off = align_up(scr.used, 256);
     const size_t rest = (scr.base != nullptr && off < scr.cap) ? scr.cap - off : 0;
@@ -529,15 +588,17 @@ sped_status apply_poly_impl(const sped_graph *g, int k, const void *V, sped_dtyp
     const sped_dtype xt_first = X0 ? x0t : vt;
     const int ldx_first = X0 ? ldx0 : ldv;
     for (int t = 0; t < steps; ++t) {
-        const void *x = t == 0 ? x_first : b[(t - 1) % 2];
+        const void *x = t == 0 ? x_first : b[(t - 1) % nb];
         sped_dtype xt = t == 0 ? xt_first : ct;
         int ldx = t == 0 ? ldx_first : ldc;
-        void *y = t == steps - 1 ? Y : b[t % 2];
+        void *y = t == steps - 1 ? Y : b[t % nb];
         sped_dtype ytt = t == steps - 1 ? yt : ct;
         int ldyy = t == steps - 1 ? ldy : ldc;
+        const void *w2 = cs[t].uses_w2 ? b[(t - 2) % nb] : nullptr;  // output of step t - 2
         step_scr.used = 0;
-        SPED_TRY(launch_poly_step(g, k, x, xt, ldx, cs[t].uses_v ? V : nullptr, vt, ldv, y, ytt,
-                                  ldyy, cs[t].alpha, cs[t].beta, cs[t].gamma, 0, step_scr, st));
+        SPED_TRY(launch_poly_step_w2(g, k, x, xt, ldx, cs[t].uses_v ? V : nullptr, vt, ldv, y,
+                                     ytt, ldyy, cs[t].alpha, cs[t].beta, cs[t].gamma, w2, ldc,
+                                     cs[t].delta, 0, step_scr, st));
     }
     return SPED_OK;
 }

@@ -196,3 +196,47 @@ def test_invalid_csr_rejected():
     rp_bad[10] = rp_bad[11] + 5  # not monotone
     with pytest.raises(sped.SpedError):
         sped.Graph(rp_bad, ci)
+
+
+@pytest.mark.parametrize("ell", [1, 2, 3, 4, 9, 24])
+@pytest.mark.parametrize("ct,tol", [(torch.float64, 1e-12), (torch.float32, 1e-5)])
+@pytest.mark.parametrize("gname", ["ragged_w", "sbm"])
+def test_chebyshev_series_matches_oracle(ell, ct, tol, gname):
+    # Clenshaw chain (three buffers, the step before last added back) against the oracle's
+    # three-term recurrence; the interval covers only part of the spectrum, so the cosh
+    # branch of T_j occurs too
+    g = GRAPHS[gname]()
+    G = sped.Graph.from_csr(g)
+    lam_b = G.info().lambda_bound
+    c = np.random.default_rng(ell).standard_normal(ell + 1) / (1.0 + np.arange(ell + 1)) ** 2
+    a, b = 0.05 * lam_b, 0.6 * lam_b
+    G.set_polynomial(sped.POLY_CHEBYSHEV, ell, eps=a, coeffs=c, lambda_star=b)
+    k = 5
+    V0 = gen.gaussian_block(g.n, k, seed=ell + 40)
+    V = to_block(V0, torch.float64 if ct == torch.float64 else torch.float32)
+    Y = sped.alloc_block(g.n, k, torch.float64, DEV)
+    sped.apply_poly(G, V, Y, k, chain_dtype=ct)
+    torch.cuda.synchronize()
+    Vs = stored(V0, V.dtype)
+    want = oracle.poly_chebyshev(g, Vs, c, a, b)
+    assert rel(host(Y, k), want) <= tol
+
+
+def test_chebyshev_power_coefficients():
+    g = GRAPHS["sbm"]()
+    G = sped.Graph.from_csr(g)
+    c = np.array([0.5, -0.25, 0.125, 0.7, -0.3])
+    a, b = 1.0, 9.0
+    G.set_polynomial(sped.POLY_CHEBYSHEV, 4, eps=a, coeffs=c, lambda_star=b)
+    # sum_j c_j T_j(al x + be) in powers of x, by evaluating at 5 points and solving
+    xs = np.linspace(0.0, 10.0, 5)
+    vals = oracle.chebyshev_scalar(c, (2.0 * xs - (a + b)) / (b - a))
+    want = np.linalg.solve(np.vander(xs, 5, increasing=True), vals)
+    assert np.allclose(G.power_coeffs(), want, rtol=1e-9, atol=1e-12)
+
+
+def test_chebyshev_rejects_empty_interval():
+    G = sped.Graph.from_csr(GRAPHS["sbm"]())
+    with pytest.raises(sped.SpedError):
+        G.set_polynomial(sped.POLY_CHEBYSHEV, 3, eps=5.0, coeffs=[1.0, 0.0, 0.0, 1.0],
+                         lambda_star=2.0)
