@@ -761,6 +761,37 @@ def run_ours(args, rank, world, local_rank):
     e2e = {"value": world * step_b / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s",
            "h2d_bytes_per_step": vb, "d2h_bytes_per_step": vb, "ms_per_step": e2e_ms}
 
+    # the same step captured once in a CUDA graph and replayed (launch gaps removed)
+    graph_rec = None
+    try:
+        opts.ev_chain_begin = None
+        opts.ev_chain_end = None
+        sped.eig_step(G, V, k, opts, scratch=scr)  # refresh the shadow after the e2e steps
+        opts.shadow_valid = 1
+        cg = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream()
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            sped.eig_step(G, V, k, opts, scratch=scr)  # warm the side stream
+        stream.wait_stream(side)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(cg):
+            sped.eig_step(G, V, k, opts, scratch=scr)
+        for _ in range(3):
+            cg.replay()
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        for _ in range(K):
+            cg.replay()
+        g1.record(stream)
+        g1.synchronize()
+        gms = g0.elapsed_time(g1) / K
+        graph_rec = {"ms_per_step": gms, "value": world * step_b / (gms * 1e-3) / 1e9,
+                     "unit": "GB/s", "launches_per_replay": ell + 4}
+    except Exception as exc:  # capture is optional: report why it was skipped
+        graph_rec = {"skipped": f"{type(exc).__name__}: {exc}"}
+
     extra = {}
     if rank == 0 and not args.no_extra:
         # gathered bytes of one chain step (every stored entry pulls one k-column row)
@@ -796,6 +827,7 @@ def run_ours(args, rank, world, local_rank):
             "roofline": roofline, "e2e": e2e, "clocks": clocks,
             "gpu_launches": K * (ell + 4),
             "poly_gbs": chain_b / (mean_chain_ms * 1e-3) / 1e9,
+            "cuda_graph_replay": graph_rec,
             "step_bytes": step_b}
     line.update(extra)
     if not args.no_cpu:
