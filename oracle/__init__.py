@@ -12,7 +12,8 @@ arXiv 2207.14589. Section, equation and table numbers below refer to it.
 
 Pinned against the paper and the mathematics by ``tests/test_oracle_*.py`` (closed-form
 spectra, L 1 = 0, the cut identity of Eq. 1, Table 1, exhaustive walk enumeration,
-eigenvector preservation, finite differences, Philox known-answer vectors). Functions with
+eigenvector preservation, finite differences, Philox known-answer vectors, exhaustive
+enumeration of edge minibatches). Functions with
 no such pin say "parity unpinned" in their docstring.
 """
 from __future__ import annotations
@@ -54,6 +55,9 @@ def lib():
                                         ctypes.c_uint32, ctypes.c_uint32, i64,
                                         ctypes.POINTER(ctypes.c_uint32)]
         L.orc_bounded_draws.restype = None
+        L.orc_first_draws.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                      ctypes.c_uint32, i64, ctypes.POINTER(ctypes.c_uint32)]
+        L.orc_first_draws.restype = None
         L.orc_incidence_dot.argtypes = [i64, i64, ctypes.c_double, i64, i64, ctypes.c_double]
         L.orc_incidence_dot.restype = ctypes.c_double
         L.orc_walk_estimate.argtypes = [i64, i32p, i32p, f32p, f64p, ctypes.c_int, f64p,
@@ -343,6 +347,100 @@ def walk_exact_terms(g, V, coeffs):
         X = laplacian_apply(g, X)
         out = out + coeffs[i] * X
     return out
+
+
+# ----------------------------------------------------------------------------------------
+# Sections 2, 4.3 and 6: edges fed in minibatches (the stochastic optimisation model)
+# ----------------------------------------------------------------------------------------
+MINIBATCH_TAG = 0x4D42
+
+
+def minibatch_edge_ids(n_edges, seed, step, batch):
+    """Edge ids of the minibatch of chain multiplication ``step``: ``batch`` independent
+    uniform draws from [0, |E|) (with replacement); draw j is the first bounded draw of the
+    word stream keyed by ``seed`` with counter words (j, step, MINIBATCH_TAG)."""
+    out = np.empty(int(batch), dtype=np.uint32)
+    if batch > 0:
+        lib().orc_first_draws(int(seed), int(step), MINIBATCH_TAG, int(n_edges), int(batch),
+                              _p(out, ctypes.c_uint32))
+    return out.astype(np.int64)
+
+
+def minibatch_edges(g, seed, step, batch):
+    """The sampled edges (a_j < b_j, weight w_j) of that minibatch, edges numbered as in
+    ``edge_list`` (the CSR order of their upper entries)."""
+    a, b, w = edge_list(g)
+    ids = minibatch_edge_ids(len(a), seed, step, batch)
+    return a[ids], b[ids], w[ids]
+
+
+def minibatch_laplacian_apply(n_edges, X, a, b, w):
+    """L_hat X for one edge sample: L_hat = (|E| / B) sum_j w_j x_j x_j^T with x_j = e_{a_j} -
+    e_{b_j}. The Laplacian is the sum of the edges' outer products (Section 4.3, weighted as
+    at the end of Section 2.1), and each draw picks an edge with probability 1/|E|, so
+    E[L_hat] = L."""
+    X = np.asarray(X, dtype=np.float64)
+    B = len(a)
+    if B < 1:
+        raise ValueError("minibatch of no edges")
+    d = (X[a] - X[b]) * (np.asarray(w, dtype=np.float64) * (n_edges / B))[:, None]
+    Y = np.zeros_like(X)
+    np.add.at(Y, a, d)
+    np.add.at(Y, b, -d)
+    return Y
+
+
+def minibatch_operator(g, seed, batch):
+    """(t, X) -> L_hat_t X, each multiplication t with the minibatch drawn for it."""
+    a, b, w = edge_list(g)
+    m = len(a)
+
+    def apply(t, X):
+        ids = minibatch_edge_ids(m, seed, t, batch)
+        return minibatch_laplacian_apply(m, X, a[ids], b[ids], w[ids])
+    return apply
+
+
+def stochastic_limit(V, s, ell, Lhat):
+    """(I - sL)^ell V with factor t (t = 0 applied first) replaced by I - s L_hat_t. With the
+    factors' samples independent, the expectation of the product is the product of the
+    expectations: (I - sL)^ell V (Table 2 limit row)."""
+    Z = np.array(V, dtype=np.float64)
+    for t in range(ell):
+        Z = Z - s * Lhat(t, Z)
+    return Z
+
+
+def stochastic_horner(V, h, shift, Lhat):
+    """sum_j h_j (L + shift I)^j V by Horner's rule (Z = h_l V; Z <- h_j V + (L + shift I) Z for
+    j = l-1..0), the t-th multiplication (evaluation order) by L_hat_t + shift I. Each
+    multiplication is independent of the Z it multiplies, so the result is unbiased."""
+    V = np.asarray(V, dtype=np.float64)
+    ell = len(h) - 1
+    Z = h[ell] * V
+    for t, j in enumerate(range(ell - 1, -1, -1)):
+        Z = h[j] * V + Lhat(t, Z) + shift * Z
+    return Z
+
+
+def stochastic_clenshaw(V, c, a, b, Lhat):
+    """sum_j c_j T_j(x) V, x = (2 L - (a + b) I) / (b - a), by Clenshaw's recurrence
+    (b_{l+1} = b_{l+2} = 0, b_j = c_j V + 2 x b_{j+1} - b_{j+2}, result c_0 V + x b_1 - b_2),
+    the t-th multiplication by x (evaluation order) using L_hat_t."""
+    V = np.asarray(V, dtype=np.float64)
+    ell = len(c) - 1
+    al, be = 2.0 / (b - a), -(a + b) / (b - a)
+    t = 0
+
+    def x(Z):
+        nonlocal t
+        out = al * Lhat(t, Z) + be * Z
+        t += 1
+        return out
+    b1, b2 = c[ell] * V, np.zeros_like(V)
+    for j in range(ell - 1, 0, -1):
+        b1, b2 = c[j] * V + 2.0 * x(b1) - b2, b1
+    return c[0] * V + x(b1) - b2
 
 
 # ----------------------------------------------------------------------------------------

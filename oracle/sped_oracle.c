@@ -167,6 +167,18 @@ void orc_bounded_draws(uint64_t seed, uint32_t a, uint32_t b, uint32_t tag, uint
     for (int64_t i = 0; i < count; ++i) out[i] = ws_bounded(&s, range);
 }
 
+/* One stream per draw: out[j] = the first bounded draw of the stream (seed, j, b, tag),
+ * j < count. The edge minibatches use this form, so every draw is independent of the others
+ * and of how many there are. */
+void orc_first_draws(uint64_t seed, uint32_t b, uint32_t tag, uint32_t range, int64_t count,
+                     uint32_t *out) {
+    for (int64_t j = 0; j < count; ++j) {
+        word_stream s;
+        ws_init(&s, seed, (uint32_t)j, b, tag);
+        out[j] = ws_bounded(&s, range);
+    }
+}
+
 /* ------------------------------------------------------------------------------------
  * Incidence algebra (Section 2, Section 4.3 Table 1). x_e has +1 at min(i,j) and -1 at
  * max(i,j); the weighted row is sqrt(w_e) x_e. The inner product of two edge rows is the
