@@ -460,6 +460,109 @@ def measure_stochastic(sped, torch, g, G, dev, stream, k, ell, reps=5, err_degre
     return out
 
 
+def measure_minibatch(sped, torch, g, G, dev, stream, k, ell, reps=5,
+                      batches=(1 << 18, 1 << 20, 1 << 22), sbm_steps=(10, 40, 100)):
+    """Edges fed in minibatches (the stochastic optimisation model of Sections 2 and 6): every
+    multiplication by L in the limit-form chain uses its own estimate (|E|/B) sum_j w x x^T from
+    B uniform edge draws. On the benchmark graph (F32 chain and blocks): time per estimate of
+    p(L) V, edges per second and the relative error against the exact F32 chain for each B;
+    the two launches of one chain step at B = 2^20 timed apart (dense pass Y = X, then the edge
+    scatter) with the scatter's algorithmic bytes per draw (edge id lookups 12 B, two X rows
+    read, two Y rows read and written by atomics). On the small SBM (N = 2,000, 4 blocks, k = 4,
+    B = |E|/4 per multiplication, FP64): mu-EG with the plain reversed Laplacian against the
+    limit form of degree 7, largest principal angle to the dense bottom-k after a few step
+    counts (a fixed step size stops at a noise floor set by the minibatch variance)."""
+    G.set_polynomial(sped.POLY_LIMIT_EXP, ell)
+    info = G.info()
+    V = sped.alloc_block(g.n, k, torch.float32, dev)
+    V[:, :k] = torch.from_numpy(gen.gaussian_block(g.n, k, seed=SEED + 41)).to(dev)
+    Yx = sped.alloc_block(g.n, k, torch.float32, dev)
+    Y = sped.alloc_block(g.n, k, torch.float32, dev)
+    mode = sped.STOCHASTIC_MINIBATCH
+    scr = torch.empty(max(sped.apply_poly_scratch_bytes(G, k, torch.float32),
+                          sped.apply_poly_scratch_bytes(G, k, torch.float32, mode)),
+                      dtype=torch.uint8, device=dev)
+    sped.apply_poly(G, V, Yx, k, chain_dtype=torch.float32, scratch=scr)
+    ynorm = float(torch.linalg.vector_norm(Yx[:, :k].double()))
+    out = {"graph_edges": info.n_edges, "degree": ell, "k": k, "dtype": "f32"}
+    seed = [SEED]
+    for B in batches:
+        def est():
+            seed[0] += 1
+            sped.apply_poly(G, V, Y, k, chain_dtype=torch.float32, mode=mode, walkers=B,
+                            seed=seed[0], scratch=scr)
+        est()
+        torch.cuda.synchronize()
+        err = float(torch.linalg.vector_norm((Y[:, :k] - Yx[:, :k]).double())) / ynorm
+        ms = _timed(torch, stream, est, reps)
+        out[f"batch_{B}"] = {"ms": ms, "edges_per_s": ell * B / (ms * 1e-3),
+                             "batch_over_edges": B / info.n_edges,
+                             "relative_error_vs_exact": err}
+    # the two launches of one step, timed apart
+    B = 1 << 20
+    a, b, wv = sped.sample_edges(G, SEED, 0, B)
+    empty = a[:0]
+    dense = lambda: sped.edge_step(g.n, V, Y, k, empty, empty, None, gamma=1.0)
+    full = lambda: sped.edge_step(g.n, V, Y, k, a, b, wv, edge_scale=info.n_edges / B,
+                                  beta=-info.scale_s, gamma=1.0)
+    dense()
+    full()
+    ms_d = _timed(torch, stream, dense, 20)
+    ms_f = _timed(torch, stream, full, 20)
+    # one chain step as the chain runs it (edges drawn inside the scatter)
+    G.set_polynomial(sped.POLY_LIMIT_EXP, 1)
+    one = lambda: sped.apply_poly(G, V, Y, k, chain_dtype=torch.float32, mode=mode, walkers=B,
+                                  seed=SEED, scratch=scr)
+    one()
+    ms_one = _timed(torch, stream, one, 20)
+    per_draw = 12 + 2 * k * 4 + 2 * 2 * k * 4
+    scatter_ms = max(ms_f - ms_d, 1e-6)
+    out["step_b1048576"] = {
+        "dense_ms": ms_d, "dense_gbs": 2 * g.n * k * 4 / (ms_d * 1e-3) / 1e9,
+        "scatter_ms": scatter_ms, "scatter_bytes_per_draw": per_draw,
+        "scatter_gbs": B * per_draw / (scatter_ms * 1e-3) / 1e9,
+        "draws_per_s": B / (scatter_ms * 1e-3),
+        "chain_step_drawn_ms": ms_one,
+        "drawn_scatter_ms": max(ms_one - ms_d, 1e-6)}
+    del scr, V, Y, Yx
+    # stochastic mu-EG on the small SBM
+    gs = gen.sbm(2000, 4, 0.05, 0.001, seed=SEED)
+    n, ks = gs.n, 4
+    Ld = np.zeros((n, n))
+    rows = np.repeat(np.arange(n), np.diff(gs.row_ptr))
+    Ld[rows, gs.col_idx] = -1.0
+    Ld[np.arange(n), np.arange(n)] = -Ld.sum(axis=1)
+    lam, U = np.linalg.eigh(Ld)
+    Ud = sped.alloc_block(n, ks, torch.float64, dev)
+    Ud[:, :ks] = torch.from_numpy(U[:, :ks]).to(dev)
+    Gs = sped.Graph.from_csr(gs, device=dev)
+    Bs = Gs.info().n_edges // 4
+    V0 = torch.from_numpy(gen.gaussian_block(n, ks, seed=SEED + 43)).to(dev)
+    sb = {"graph": "sbm_n2000_b4_k4", "batch": Bs, "edges": Gs.info().n_edges}
+    for name, poly, eta in (("plain_mu_eg", ("shift", 1), None),
+                            ("limit7_mu_eg", ("limit", 7), 0.5)):
+        inf = (Gs.set_polynomial(sped.POLY_LIMIT_EXP, 7) if poly[0] == "limit"
+               else Gs.set_polynomial(sped.POLY_SHIFT, 1))
+        e = eta if eta is not None else 2.0 / inf.lambda_star
+        opts = sped.step_opts(sped.MU_EG, e, torch.float64, torch.float64, mode=mode, walkers=Bs,
+                              seed=SEED)
+        scr = torch.empty(sped.eig_step_scratch_bytes(Gs, opts, ks), dtype=torch.uint8,
+                          device=dev)
+        Vb = sped.alloc_block(n, ks, torch.float64, dev)
+        Vb[:, :ks] = V0
+        rec = {"eta": e, "degree": inf.degree}
+        for t in range(1, max(sbm_steps) + 1):
+            opts.seed = SEED + 7919 * t
+            sped.eig_step(Gs, Vb, ks, opts, scratch=scr)
+            if t in sbm_steps:
+                rec[f"angle_step_{t}"] = _principal_angle(sped, Ud, Vb, ks)
+        rec["edges_per_step"] = Bs * inf.degree
+        sb[name] = rec
+    out["sbm_mu_eg"] = sb
+    G.set_polynomial(sped.POLY_LIMIT_EXP, ell)
+    return out
+
+
 def measure_degree_sweep(sped, torch, dev, stream, k=4, cap=200,
                          degrees=(11, 51, 151, 251)):
     """The limit form's degree threshold (cliques graphs of Section 5.4): four 450-cliques joined
@@ -797,6 +900,7 @@ def run_ours(args, rank, world, local_rank):
         # gathered bytes of one chain step (every stored entry pulls one k-column row)
         extra["gather_bytes_per_launch"] = g.nnz * k * 2
         extra["stochastic"] = measure_stochastic(sped, torch, g, G, dev, stream, k, ell)
+        extra["minibatch"] = measure_minibatch(sped, torch, g, G, dev, stream, k, ell)
         extra["differentiable"] = measure_differentiable(sped, torch, dev, stream)
         extra["batched"] = measure_batched(sped, torch, dev, stream, n_graphs=args.batched_graphs)
         extra["permuted_node_order"] = measure_permuted(sped, torch, dev, stream, k, ell)

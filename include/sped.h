@@ -63,9 +63,10 @@ typedef enum {
 } sped_poly_kind;
 
 typedef enum {
-    SPED_EXACT = 0,            /* chained SpMM                                           */
-    SPED_STOCHASTIC_IS = 1,    /* random-walk estimate, importance weights (Section 4.3) */
-    SPED_STOCHASTIC_REJECT = 2 /* random-walk estimate, the text's rejection step        */
+    SPED_EXACT = 0,               /* chained SpMM                                           */
+    SPED_STOCHASTIC_IS = 1,       /* random-walk estimate, importance weights (Section 4.3) */
+    SPED_STOCHASTIC_REJECT = 2,   /* random-walk estimate, the text's rejection step        */
+    SPED_STOCHASTIC_MINIBATCH = 3 /* every multiplication by L from its own edge minibatch  */
 } sped_mode;
 
 typedef enum { SPED_SOLVER_MU_EG = 0, SPED_SOLVER_OJA = 1 } sped_solver;
@@ -186,9 +187,20 @@ sped_status sped_set_schedule(sped_graph *g, int split, int merge_ipg);
  * Y = M V for the graph's polynomial M (Sections 4.2-4.3).
  *  mode SPED_EXACT: the chain of poly steps; intermediate products stored as chain_t
  *    (BF16 halves gather traffic, accumulation stays F32), the last step writes y_t.
- *  mode SPED_STOCHASTIC_*: Y = c_0 V + mean over `walkers` walks of the sampled terms
- *    (Section 4.3), draws from Philox4x32-10 keyed by seed (documented in walk.cu);
+ *  mode SPED_STOCHASTIC_IS / _REJECT: Y = c_0 V + mean over `walkers` walks of the sampled
+ *    terms (Section 4.3), draws from Philox4x32-10 keyed by seed (documented in walk.cu);
  *    y_t must be F32 or F64; chain_t is ignored.
+ *  mode SPED_STOCHASTIC_MINIBATCH: the edges-in-minibatches model of Sections 2 and 6. The
+ *    chain of the exact mode runs with multiplication t (factor t of the limit form, step t of
+ *    Horner's or Clenshaw's recurrence, t = 0, 1, ... in evaluation order) by its own estimate
+ *    L_hat_t = (|E| / B) sum_{j<B} w_{e_j} x_{e_j} x_{e_j}^T, where B = `walkers` and the e_j are
+ *    edge ids drawn uniformly with replacement (L = sum_e w_e x_e x_e^T, Section 4.3). Draw j of
+ *    multiplication t is the first Lemire bounded draw in [0, |E|) of the Philox4x32-10 word
+ *    stream with key `seed` and counters (j, t, 0x4D42, i), i = 0, 1, ... (edges numbered as in
+ *    sped_graph_edges). The multiplications are independent, so Y is an unbiased estimate of
+ *    M V for every family. chain_t, v_t and y_t: F32 or F64 (the edge terms are added by
+ *    atomic adds, so the summation order is not fixed: results match a sequential sum to
+ *    rounding, not bit for bit). 1 <= B <= 2^32.
  * ------------------------------------------------------------------------------------ */
 sped_status sped_apply_poly(const sped_graph *g, int k, const void *d_V, sped_dtype v_t, int ldv,
                             void *d_Y, sped_dtype y_t, int ldy, sped_dtype chain_t,
@@ -197,6 +209,31 @@ sped_status sped_apply_poly(const sped_graph *g, int k, const void *d_V, sped_dt
 
 sped_status sped_apply_poly_scratch_size(const sped_graph *g, int k, sped_dtype chain_t,
                                          sped_mode mode, size_t *bytes);
+
+/* ------------------------------------------------------------------------------------
+ * Edge minibatches fed from outside (Sections 2 and 6: edges arrive in minibatches, or are
+ * drawn from a distribution such as a link-prediction model's output).
+ * sped_sample_edges writes the minibatch that SPED_STOCHASTIC_MINIBATCH uses for
+ * multiplication `step`: for draw j < count, d_a[j] < d_b[j] are the edge's endpoints and
+ * d_w[j] its weight (1 for an unweighted graph); any output may be NULL. count <= 2^32, and the
+ * graph must have an edge when count > 0.
+ * sped_edge_step runs one chain step on a caller-supplied minibatch:
+ *   Y = alpha V + gamma X + beta * edge_scale * sum_{j<count} w_j x_j x_j^T X,
+ * x_j = e_{a_j} - e_{b_j}; that is Y[a_j] += c_j (X[a_j] - X[b_j]) and Y[b_j] -= c_j (X[a_j] -
+ * X[b_j]) with c_j = beta * edge_scale * w_j. d_w may be NULL (all weights 1). edge_scale =
+ * |E| / count makes the sum an unbiased estimate of L X when the edges are uniform draws from E.
+ * X, V, Y: n x k blocks, F32 or F64; X and Y must not overlap; d_V may be NULL when alpha == 0.
+ * Draws with an endpoint outside [0, n) are skipped and counted into *d_skipped (device int32,
+ * may be NULL). The edge terms are added by atomic adds (order not fixed).
+ * ------------------------------------------------------------------------------------ */
+sped_status sped_sample_edges(const sped_graph *g, uint64_t seed, uint32_t step, int64_t count,
+                              int32_t *d_a, int32_t *d_b, float *d_w, void *stream);
+
+sped_status sped_edge_step(int64_t n, int k, const int32_t *d_a, const int32_t *d_b,
+                           const float *d_w, int64_t count, double edge_scale, const void *d_X,
+                           sped_dtype x_t, int ldx, const void *d_V, sped_dtype v_t, int ldv,
+                           void *d_Y, sped_dtype y_t, int ldy, double alpha, double beta,
+                           double gamma, int32_t *d_skipped, void *stream);
 
 /* ------------------------------------------------------------------------------------
  * Gram of a tall-skinny pair: G = [A B]^T [A B], (ka+kb) x (ka+kb) row-major FP64,
@@ -244,7 +281,7 @@ typedef struct {
     sped_dtype chain_t; /* storage of intermediate products                           */
     sped_dtype y_t;     /* storage of Y = M V: F32 or F64                              */
     sped_mode mode;     /* exact or stochastic p(L) V                                  */
-    int64_t walkers;
+    int64_t walkers;    /* walks (IS / REJECT) or edges per minibatch (MINIBATCH)        */
     uint64_t seed;
     /* optional cudaEvent_t pair (as void*, NULL = none) recorded on the stream immediately
      * before and after the p(L) V chain, for live timing of the dominant kernel */
@@ -294,7 +331,8 @@ sped_status sped_rayleigh_ritz_scratch_size(const sped_graph *g, int k, size_t *
  * tracks the sine of the angle between span(V) and span(MV). Phase 1 stores the chain in
  * opts.step.chain_t (e.g. BF16) until the measure is <= switch_tol or phase1_steps steps;
  * phase 2 uses refine_chain_t (e.g. F32) until <= tol. The test reads the statistics every
- * check_every steps. h_lambda (host, k doubles, may be NULL) receives the
+ * check_every steps. In the stochastic modes step s (from 1) draws with seed opts.step.seed +
+ * s - 1, so the estimates of different steps are independent. h_lambda (host, k doubles, may be NULL) receives the
  * Rayleigh quotients of L.
  * ------------------------------------------------------------------------------------ */
 typedef struct {

@@ -21,7 +21,7 @@ OK, ERR_INVALID_ARG, ERR_BAD_CSR, ERR_UNSUPPORTED, ERR_NUMERIC, ERR_NOT_CONVERGE
     ERR_TIMEOUT, ERR_CUDA, ERR_SCRATCH = range(9)
 BF16, F32, F64 = 0, 1, 2
 POLY_LIMIT_EXP, POLY_TAYLOR_EXP, POLY_TAYLOR_LOG, POLY_MONOMIAL, POLY_SHIFT, POLY_CHEBYSHEV = range(6)
-EXACT, STOCHASTIC_IS, STOCHASTIC_REJECT = range(3)
+EXACT, STOCHASTIC_IS, STOCHASTIC_REJECT, STOCHASTIC_MINIBATCH = range(4)
 MU_EG, OJA = 0, 1
 
 _STATUS = {0: "OK", 1: "INVALID_ARG", 2: "BAD_CSR", 3: "UNSUPPORTED", 4: "NUMERIC",
@@ -117,6 +117,9 @@ def lib():
         "sped_autotune_scratch_size": [vp, i32, i32, P(sz)],
         "sped_autotune": [vp, i32, i32, vp, sz, vp, P(sped_tune_report)],
         "sped_set_schedule": [vp, i32, i32],
+        "sped_sample_edges": [vp, u64, ctypes.c_uint32, i64, vp, vp, vp, vp],
+        "sped_edge_step": [i64, i32, vp, vp, vp, i64, dbl, vp, i32, i32, vp, i32, i32, vp, i32,
+                           i32, dbl, dbl, dbl, vp, vp],
     }
     for name, args in sigs.items():
         f = getattr(L, name)
@@ -316,6 +319,38 @@ def apply_poly(g: Graph, V, Y, k, chain_dtype=None, mode=EXACT, walkers=0, seed=
     _check(lib().sped_apply_poly(g.handle, k, _ptr(V), vt, ldv, _ptr(Y), yt, ldy, ct, mode,
                                  int(walkers), int(seed), _ptr(scratch), scratch.numel(),
                                  _stream(stream)))
+    return Y
+
+
+def sample_edges(g: Graph, seed, step, count, stream=None):
+    """The edge minibatch that STOCHASTIC_MINIBATCH draws for multiplication `step`:
+    (a, b, w) device tensors (int32, int32, float32) of length count, a < b."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    a = torch.empty(max(int(count), 1), dtype=torch.int32, device=dev)
+    b = torch.empty_like(a)
+    w = torch.empty(max(int(count), 1), dtype=torch.float32, device=dev)
+    _check(lib().sped_sample_edges(g.handle, int(seed), int(step), int(count), _ptr(a), _ptr(b),
+                                   _ptr(w), _stream(stream)))
+    return a[:count], b[:count], w[:count]
+
+
+def edge_step(n, X, Y, k, a, b, w=None, edge_scale=1.0, alpha=0.0, beta=1.0, gamma=0.0, V=None,
+              skipped=None, stream=None):
+    """Y = alpha V + gamma X + beta * edge_scale * sum_j w_j x_j x_j^T X for the caller's edge
+    minibatch (a, b, w: int32 / int32 / float32 device tensors)."""
+    xt, ldx = _block(X, k)
+    yt, ldy = _block(Y, k)
+    vt, ldv = _block(V, k) if V is not None else (F32, k)
+    for t, dt in ((a, torch.int32), (b, torch.int32)) + (((w, torch.float32),) if w is not None
+                                                         else ()):
+        if t.dtype != dt or not t.is_contiguous():
+            raise TypeError("edge arrays: contiguous int32 endpoints, float32 weights")
+        if t.numel() != a.numel():
+            raise ValueError("edge arrays of different lengths")
+    _check(lib().sped_edge_step(int(n), k, _ptr(a), _ptr(b), _ptr(w), int(a.numel()),
+                                float(edge_scale), _ptr(X), xt, ldx, _ptr(V), vt, ldv, _ptr(Y), yt,
+                                ldy, float(alpha), float(beta), float(gamma), _ptr(skipped),
+                                _stream(stream)))
     return Y
 
 

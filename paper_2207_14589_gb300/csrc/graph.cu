@@ -239,7 +239,8 @@ __global__ void k_reverse(int64_t n, int64_t nnz, const int32_t *rp, const int32
 // Undirected edge ids: upper entries numbered in CSR order; lower entries take the id of
 // their reverse entry.
 __global__ void k_edges(int64_t n, const int32_t *rp, const int32_t *ci, const int32_t *rev,
-                        const int32_t *eoff, int32_t *eid, int32_t *edge_p, int32_t *edge_a) {
+                        const int32_t *eoff, int32_t *eid, int32_t *edge_p, int32_t *edge_a,
+                        int2 *edge_ab) {
     int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
     int p0 = rp[r], p1 = rp[r + 1];
@@ -251,6 +252,7 @@ __global__ void k_edges(int64_t n, const int32_t *rp, const int32_t *ci, const i
             eid[rev[p]] = e;
             edge_p[e] = p;
             edge_a[e] = (int)r;
+            edge_ab[e] = make_int2((int)r, c);
             ++e;
         }
     }
@@ -280,7 +282,7 @@ __global__ void k_edge_ends(int64_t ne, const int32_t *ci, const int32_t *edge_p
 static unsigned nblocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 struct WsLayout {
-    size_t rev, eid, edge_p, edge_a, eoff, ws_w, bsum, stats, total;
+    size_t rev, eid, edge_p, edge_a, edge_ab, eoff, ws_w, bsum, stats, total;
 };
 
 static WsLayout ws_layout(int64_t n, int64_t nnz) {
@@ -290,6 +292,7 @@ static WsLayout ws_layout(int64_t n, int64_t nnz) {
     L.eid = p.used; p.add(sizeof(int32_t) * nnz); p.used = align_up(p.used, 256);
     L.edge_p = p.used; p.add(sizeof(int32_t) * (nnz / 2 + 1)); p.used = align_up(p.used, 256);
     L.edge_a = p.used; p.add(sizeof(int32_t) * (nnz / 2 + 1)); p.used = align_up(p.used, 256);
+    L.edge_ab = p.used; p.add(sizeof(int2) * (nnz / 2 + 1)); p.used = align_up(p.used, 256);
     L.eoff = p.used; p.add(sizeof(int32_t) * (n + 1)); p.used = align_up(p.used, 256);
     L.ws_w = p.used; p.add(sizeof(float) * nnz); p.used = align_up(p.used, 256);
     L.bsum = p.used; p.add(sizeof(int32_t) * scan_sums_elems(n + 1)); p.used = align_up(p.used, 256);
@@ -405,6 +408,7 @@ sped_status sped_build_laplacian(int64_t n, int64_t nnz, const int32_t *d_row_pt
     char *ws = (char *)d_workspace;
     int32_t *rev = (int32_t *)(ws + L.rev), *eid = (int32_t *)(ws + L.eid);
     int32_t *edge_p = (int32_t *)(ws + L.edge_p), *edge_a = (int32_t *)(ws + L.edge_a);
+    int2 *edge_ab = (int2 *)(ws + L.edge_ab);
     int32_t *eoff = (int32_t *)(ws + L.eoff), *bsum = (int32_t *)(ws + L.bsum);
     SetupStats *stats = (SetupStats *)(ws + L.stats);
     SetupStats h;
@@ -437,7 +441,7 @@ sped_status sped_build_laplacian(int64_t n, int64_t nnz, const int32_t *d_row_pt
     if ((int64_t)n_edges * 2 != nnz)
         return fail(SPED_ERR_BAD_CSR, "upper entries %d != nnz/2", n_edges);
     k_edges<<<nblocks(n, 256), 256, 0, st>>>(n, d_row_ptr, d_col_idx, rev, eoff, eid, edge_p,
-                                             edge_a);
+                                             edge_a, edge_ab);
     SPED_CHECK_LAUNCH("k_edges");
     SPED_CUDA(cudaStreamSynchronize(st));
 
@@ -453,6 +457,7 @@ sped_status sped_build_laplacian(int64_t n, int64_t nnz, const int32_t *d_row_pt
     g->eid = eid;
     g->edge_p = edge_p;
     g->edge_a = edge_a;
+    g->edge_ab = edge_ab;
     g->eoff = eoff;
     g->ws_w = (float *)(ws + L.ws_w);
     g->stats = stats;

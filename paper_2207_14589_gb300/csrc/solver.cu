@@ -808,6 +808,7 @@ sped_status sped_solve_bottom_k(const sped_graph *g, const sped_solve_opts *opts
     for (int step = 1; step <= opts->max_steps; ++step) {
         sped_step_opts so = phase_opts(opts, phase);
         if (step > 1) so.shadow_valid = 1;  // the previous step left bf16(V) in the shadow
+        if (so.mode != SPED_EXACT) so.seed += (uint64_t)(step - 1);  // fresh draws every step
         // the statistics (Rayleigh quotients, residuals, step norms) cost a Cholesky solve and a
         // second k x k product per row, so they are formed on check steps only
         const bool check = step % opts->check_every == 0 || step == opts->max_steps;

@@ -105,6 +105,7 @@ struct sped_graph {
     int32_t *eid;         // undirected edge id of entry p
     int32_t *edge_p;      // entry position (row a, col b, a < b) of edge e
     int32_t *edge_a;      // row a of edge e
+    int2 *edge_ab;        // (a, b) of edge e in one 8-byte word (one load per sampled edge)
     int32_t *eoff;        // first edge id of row r (n+1)
     float *ws_w;          // workspace copy for weights set per edge
     void *stats;          // small device statistics slot inside the workspace
@@ -309,5 +310,24 @@ sped_status launch_walk(const sped_graph *g, int k, const void *V, sped_dtype vt
                         sped_dtype yt, int ldy, sped_mode mode, int64_t walkers, uint64_t seed,
                         cudaStream_t st);
 sped_status check_layout(const void *p, sped_dtype t, int k, int ld, const char *name);
+
+// One edge minibatch: drawn from a graph's edges (graph != NULL: draws j < count of
+// multiplication `step`, seed as documented in minibatch.cu) or given by the caller's arrays.
+struct EdgeBatch {
+    const sped_graph *graph = nullptr;
+    uint64_t seed = 0;
+    uint32_t step = 0;
+    int64_t count = 0;
+    double scale = 1.0;  // |E| / count for uniform draws
+    const int32_t *a = nullptr, *b = nullptr;
+    const float *w = nullptr;
+    int32_t *skipped = nullptr;
+};
+// Y = alpha V + gamma X + delta W2 + beta * scale * sum_j w_j x_j x_j^T X (X, V, W2, Y: F32 or
+// F64; W2 of X's type; V and W2 may be NULL)
+sped_status launch_edge_step(int64_t n, int k, const void *X, sped_dtype xt, int ldx,
+                             const void *V, sped_dtype vt, int ldv, const void *W2, int ldw2,
+                             double delta, void *Y, sped_dtype yt, int ldy, double alpha,
+                             double beta, double gamma, const EdgeBatch &eb, cudaStream_t st);
 
 }  // namespace sped

@@ -548,11 +548,12 @@ static int chain_buffers(const std::vector<StepCoef> &cs) {
 }
 
 size_t apply_poly_scratch(const sped_graph *g, int k, sped_dtype ct, sped_mode mode) {
-    if (mode != SPED_EXACT) return 0;
+    if (mode != SPED_EXACT && mode != SPED_STOCHASTIC_MINIBATCH) return 0;
     const int nbuf = chain_buffers(chain_coefs(g->poly));
     ScratchPlan p;
     size_t buf = (size_t)g->n * padded_ld(k, ct) * dtype_size(ct);
     for (int i = 0; i < nbuf; ++i) p.add(buf);
+    if (mode == SPED_STOCHASTIC_MINIBATCH) return p.total();
     size_t ms = 0;
     for (sped_dtype t : {SPED_BF16, SPED_F32, SPED_F64}) {
         size_t x = poly_step_scratch(g, k, t, 0);
@@ -566,8 +567,20 @@ sped_status apply_poly_impl(const sped_graph *g, int k, const void *V, sped_dtyp
                             void *Y, sped_dtype yt, int ldy, sped_dtype ct, sped_mode mode,
                             int64_t walkers, uint64_t seed, Scratch &scr, cudaStream_t st,
                             const void *X0, sped_dtype x0t, int ldx0) {
-    if (mode != SPED_EXACT)
+    if (mode == SPED_STOCHASTIC_IS || mode == SPED_STOCHASTIC_REJECT)
         return launch_walk(g, k, V, vt, ldv, Y, yt, ldy, mode, walkers, seed, st);
+    const bool minibatch = mode == SPED_STOCHASTIC_MINIBATCH;
+    if (mode != SPED_EXACT && !minibatch)
+        return fail(SPED_ERR_INVALID_ARG, "apply_poly: mode %d", (int)mode);
+    if (minibatch) {
+        if (walkers < 1 || walkers > (int64_t)UINT32_MAX + 1)
+            return fail(SPED_ERR_INVALID_ARG, "minibatch: %lld edges per batch not in 1..2^32",
+                        (long long)walkers);
+        if (ct == SPED_BF16)
+            return fail(SPED_ERR_UNSUPPORTED, "minibatch: the chain accumulates by atomic adds, "
+                                              "chain dtype must be F32 or F64");
+        X0 = nullptr;  // the first multiplication reads V itself
+    }
     std::vector<StepCoef> cs = chain_coefs(g->poly);
     const int steps = (int)cs.size();
     const int ldc = padded_ld(k, ct);
@@ -595,6 +608,18 @@ sped_status apply_poly_impl(const sped_graph *g, int k, const void *V, sped_dtyp
         sped_dtype ytt = t == steps - 1 ? yt : ct;
         int ldyy = t == steps - 1 ? ldy : ldc;
         const void *w2 = cs[t].uses_w2 ? b[(t - 2) % nb] : nullptr;  // output of step t - 2
+        if (minibatch) {
+            EdgeBatch eb;
+            eb.graph = g->n_edges > 0 ? g : nullptr;  // no edges: L = 0, nothing to add
+            eb.seed = seed;
+            eb.step = (uint32_t)t;
+            eb.count = g->n_edges > 0 ? walkers : 0;
+            eb.scale = (double)g->n_edges / (double)walkers;
+            SPED_TRY(launch_edge_step(g->n, k, x, xt, ldx, cs[t].uses_v ? V : nullptr, vt, ldv,
+                                      w2, ldc, cs[t].delta, y, ytt, ldyy, cs[t].alpha,
+                                      cs[t].beta, cs[t].gamma, eb, st));
+            continue;
+        }
         step_scr.used = 0;
         SPED_TRY(launch_poly_step_w2(g, k, x, xt, ldx, cs[t].uses_v ? V : nullptr, vt, ldv, y,
                                      ytt, ldyy, cs[t].alpha, cs[t].beta, cs[t].gamma, w2, ldc,
@@ -648,7 +673,8 @@ sped_status sped_apply_poly(const sped_graph *g, int k, const void *d_V, sped_dt
     SPED_TRY(check_layout(d_V, v_t, k, ldv, "apply_poly V"));
     SPED_TRY(check_layout(d_Y, y_t, k, ldy, "apply_poly Y"));
     if (!dtype_valid(chain_t)) return fail(SPED_ERR_INVALID_ARG, "apply_poly: chain dtype");
-    if (mode != SPED_EXACT && mode != SPED_STOCHASTIC_IS && mode != SPED_STOCHASTIC_REJECT)
+    if (mode != SPED_EXACT && mode != SPED_STOCHASTIC_IS && mode != SPED_STOCHASTIC_REJECT &&
+        mode != SPED_STOCHASTIC_MINIBATCH)
         return fail(SPED_ERR_INVALID_ARG, "apply_poly: mode %d", (int)mode);
     if (d_V == d_Y) return fail(SPED_ERR_INVALID_ARG, "apply_poly: V and Y must not alias");
     Scratch scr(d_scratch, scratch_bytes);

@@ -79,3 +79,21 @@ def test_mixed_eig_step_full_size(sbm_n1e6):
     Yp = Y + tol * np.linalg.norm(Y) * D / np.linalg.norm(D)
     gain = rel(oracle.mu_eg_step(Vs, Yp, 1.0), want) / tol
     assert rel(host(V, K), want) <= 1.5 * tol * max(1.0, gain)
+
+
+def test_minibatch_chain_full_size(sbm_n1e6):
+    # the edge-minibatch chain at full size, 2^20 edges per multiplication (the benchmark's
+    # minibatch), F32 chain: three factors of (I - s L_hat_t) against the oracle's draws
+    g, G, _ = sbm_n1e6
+    Gm = sped.Graph.from_csr(g)
+    s, ell, B, seed = 1.0 / 41, 3, 1 << 20, 20220729
+    Gm.set_polynomial(sped.POLY_LIMIT_EXP, ell, scale=s)
+    V0 = gen.gaussian_block(N, K, seed=8)
+    V = to_block(V0, torch.float32)
+    Y = sped.alloc_block(N, K, torch.float32, DEV)
+    sped.apply_poly(Gm, V, Y, K, chain_dtype=torch.float32, mode=sped.STOCHASTIC_MINIBATCH,
+                    walkers=B, seed=seed)
+    torch.cuda.synchronize()
+    want = oracle.stochastic_limit(stored(V0, torch.float32), s, ell,
+                                   oracle.minibatch_operator(g, seed, B))
+    assert rel(host(Y, K), want) <= 1e-5
