@@ -58,6 +58,10 @@ def lib():
         L.orc_first_draws.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                       ctypes.c_uint32, i64, ctypes.POINTER(ctypes.c_uint32)]
         L.orc_first_draws.restype = None
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        L.orc_stratified_draws.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                           i64, i64, i64p, i64p]
+        L.orc_stratified_draws.restype = None
         L.orc_incidence_dot.argtypes = [i64, i64, ctypes.c_double, i64, i64, ctypes.c_double]
         L.orc_incidence_dot.restype = ctypes.c_double
         L.orc_walk_estimate.argtypes = [i64, i32p, i32p, f32p, f64p, ctypes.c_int, f64p,
@@ -366,6 +370,20 @@ def minibatch_edge_ids(n_edges, seed, step, batch):
     return out.astype(np.int64)
 
 
+def stratified_edge_ids(n_edges, seed, step, batch):
+    """Variance-reduced minibatch (the paper leaves variance reduction to future work, Section
+    6): the edge ids are cut into ``batch`` contiguous strata S_j = [floor(j|E|/B),
+    floor((j+1)|E|/B)) and draw j is uniform in S_j (first bounded draw over |S_j| of the
+    stream (seed; j, step, MINIBATCH_TAG)). Returns (ids, |S_j|); an empty stratum (B > |E|)
+    gives id -1 and size 0."""
+    ids = np.empty(int(batch), dtype=np.int64)
+    sizes = np.empty(int(batch), dtype=np.int64)
+    if batch > 0:
+        lib().orc_stratified_draws(int(seed), int(step), MINIBATCH_TAG, int(n_edges), int(batch),
+                                   _p(ids, ctypes.c_int64), _p(sizes, ctypes.c_int64))
+    return ids, sizes
+
+
 def minibatch_edges(g, seed, step, batch):
     """The sampled edges (a_j < b_j, weight w_j) of that minibatch, edges numbered as in
     ``edge_list`` (the CSR order of their upper entries)."""
@@ -390,12 +408,29 @@ def minibatch_laplacian_apply(n_edges, X, a, b, w):
     return Y
 
 
-def minibatch_operator(g, seed, batch):
-    """(t, X) -> L_hat_t X, each multiplication t with the minibatch drawn for it."""
+def stratified_laplacian_apply(X, a, b, w, sizes):
+    """L_hat X for a stratified sample: L_hat = sum_j |S_j| w_j x_j x_j^T (draw j stands for its
+    stratum: each edge of S_j is drawn with probability 1/|S_j|, so E[L_hat] = L)."""
+    X = np.asarray(X, dtype=np.float64)
+    d = (X[a] - X[b]) * (np.asarray(w, dtype=np.float64) * sizes)[:, None]
+    Y = np.zeros_like(X)
+    np.add.at(Y, a, d)
+    np.add.at(Y, b, -d)
+    return Y
+
+
+def minibatch_operator(g, seed, batch, stratified=False):
+    """(t, X) -> L_hat_t X, each multiplication t with the minibatch drawn for it (uniform
+    draws, or one draw per stratum of the edge order)."""
     a, b, w = edge_list(g)
     m = len(a)
 
     def apply(t, X):
+        if stratified:
+            ids, sizes = stratified_edge_ids(m, seed, t, batch)
+            keep = sizes > 0
+            ids, sizes = ids[keep], sizes[keep]
+            return stratified_laplacian_apply(X, a[ids], b[ids], w[ids], sizes.astype(np.float64))
         ids = minibatch_edge_ids(m, seed, t, batch)
         return minibatch_laplacian_apply(m, X, a[ids], b[ids], w[ids])
     return apply

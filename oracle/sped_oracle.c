@@ -179,6 +179,24 @@ void orc_first_draws(uint64_t seed, uint32_t b, uint32_t tag, uint32_t range, in
     }
 }
 
+/* Stratified draws: the ids 0..range-1 are cut into `count` strata S_j = [floor(j range /
+ * count), floor((j+1) range / count)); draw j is uniform in S_j (the first bounded draw of the
+ * stream (seed, j, b, tag) over |S_j|). out_id[j] = -1 and out_size[j] = 0 for an empty
+ * stratum. */
+void orc_stratified_draws(uint64_t seed, uint32_t b, uint32_t tag, int64_t range, int64_t count,
+                          int64_t *out_id, int64_t *out_size) {
+    for (int64_t j = 0; j < count; ++j) {
+        int64_t lo = (j * range) / count, hi = ((j + 1) * range) / count;
+        out_size[j] = hi - lo;
+        out_id[j] = -1;
+        if (hi > lo) {
+            word_stream s;
+            ws_init(&s, seed, (uint32_t)j, b, tag);
+            out_id[j] = lo + (int64_t)ws_bounded(&s, (uint32_t)(hi - lo));
+        }
+    }
+}
+
 /* ------------------------------------------------------------------------------------
  * Incidence algebra (Section 2, Section 4.3 Table 1). x_e has +1 at min(i,j) and -1 at
  * max(i,j); the weighted row is sqrt(w_e) x_e. The inner product of two edge rows is the

@@ -132,3 +132,59 @@ def test_sampler_and_chain_mean_converges():
     mean, se = outs.mean(0), outs.std(0, ddof=1) / np.sqrt(R)
     exact = oracle.poly_limit(g, V, s, ell)
     assert np.all(np.abs(mean - exact) <= 5.0 * se + 1e-12)
+
+
+# ---- stratified minibatches (variance reduction) ----------------------------------------
+def test_strata_partition_the_edges():
+    for m, B in [(37, 5), (37, 37), (10, 16), (1000, 7)]:
+        ids, sizes = oracle.stratified_edge_ids(m, seed=3, step=2, batch=B)
+        assert sizes.sum() == m
+        lo = np.array([j * m // B for j in range(B)])
+        assert np.all((sizes == 0) == (ids < 0))
+        nz = sizes > 0
+        assert np.all(ids[nz] >= lo[nz]) and np.all(ids[nz] < lo[nz] + sizes[nz])
+    # within one stratum the draw is uniform
+    m, B = 50, 5
+    hits = np.stack([oracle.stratified_edge_ids(m, s, 0, B)[0] for s in range(20000)])
+    counts = np.bincount(hits[:, 2], minlength=m)[20:30]
+    chi2 = float(np.sum((counts - 2000.0) ** 2 / 2000.0))
+    assert chi2 < 40.0  # 9 dof
+
+
+def test_stratified_sample_is_unbiased_exactly():
+    # every combination of one edge per stratum, each with probability prod 1/|S_j|
+    g = _tiny_weighted()
+    a, b, w = oracle.edge_list(g)
+    m, B = len(a), 3
+    X = gen.gaussian_block(g.n, 2, seed=5)
+    lo = [j * m // B for j in range(B)]
+    hi = [(j + 1) * m // B for j in range(B)]
+    sizes = np.array([h - l for l, h in zip(lo, hi)], dtype=np.float64)
+    acc, count = np.zeros_like(X), 0
+    for combo in itertools.product(*[range(l, h) for l, h in zip(lo, hi)]):
+        idx = np.array(combo)
+        acc += oracle.stratified_laplacian_apply(X, a[idx], b[idx], w[idx], sizes)
+        count += 1
+    assert count == int(np.prod(sizes))
+    assert np.allclose(acc / count, oracle.laplacian_apply(g, X), rtol=0, atol=1e-13)
+
+
+def test_one_stratum_per_edge_is_exact():
+    g = gen.uniform_edge_weights(gen.random_graph(40, 90, seed=6), seed=7)
+    m = len(oracle.edge_list(g)[0])
+    V = gen.gaussian_block(g.n, 3, seed=8)
+    for B in (m, m + 13):  # |S_j| = 1, or empty strata
+        op = oracle.minibatch_operator(g, seed=4, batch=B, stratified=True)
+        assert np.allclose(oracle.stochastic_limit(V, 0.1, 5, op), oracle.poly_limit(g, V, 0.1, 5),
+                           atol=1e-12)
+
+
+def test_stratified_chain_mean_converges():
+    g = _tiny_weighted()
+    V = gen.gaussian_block(g.n, 2, seed=7)
+    ell, s, R = 3, 0.15, 3000
+    outs = np.stack([oracle.stochastic_limit(V, s, ell,
+                                             oracle.minibatch_operator(g, r, 2, stratified=True))
+                     for r in range(R)])
+    mean, se = outs.mean(0), outs.std(0, ddof=1) / np.sqrt(R)
+    assert np.all(np.abs(mean - oracle.poly_limit(g, V, s, ell)) <= 5.0 * se + 1e-12)
