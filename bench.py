@@ -464,8 +464,10 @@ def measure_minibatch(sped, torch, g, G, dev, stream, k, ell, reps=5,
                       batches=(1 << 18, 1 << 20, 1 << 22), sbm_steps=(10, 40, 100)):
     """Edges fed in minibatches (the stochastic optimisation model of Sections 2 and 6): every
     multiplication by L in the limit-form chain uses its own estimate (|E|/B) sum_j w x x^T from
-    B uniform edge draws. On the benchmark graph (F32 chain and blocks): time per estimate of
-    p(L) V, edges per second and the relative error against the exact F32 chain for each B;
+    B uniform edge draws (or, stratified, one draw per contiguous stratum of the edge order,
+    weighted by the stratum's size). On the benchmark graph (F32 chain and blocks): time per
+    estimate of p(L) V, edges per second and the relative error against the exact F32 chain for
+    each B and both samplers;
     the two launches of one chain step at B = 2^20 timed apart (dense pass Y = X, then the edge
     scatter) with the scatter's algorithmic bytes per draw (edge id lookups 12 B, two X rows
     read, two Y rows read and written by atomics). On the small SBM (N = 2,000, 4 blocks, k = 4,
@@ -480,24 +482,27 @@ def measure_minibatch(sped, torch, g, G, dev, stream, k, ell, reps=5,
     Y = sped.alloc_block(g.n, k, torch.float32, dev)
     mode = sped.STOCHASTIC_MINIBATCH
     scr = torch.empty(max(sped.apply_poly_scratch_bytes(G, k, torch.float32),
-                          sped.apply_poly_scratch_bytes(G, k, torch.float32, mode)),
+                          sped.apply_poly_scratch_bytes(G, k, torch.float32, mode),
+                          sped.apply_poly_scratch_bytes(G, k, torch.float32,
+                                                        sped.STOCHASTIC_MINIBATCH_STRATIFIED)),
                       dtype=torch.uint8, device=dev)
     sped.apply_poly(G, V, Yx, k, chain_dtype=torch.float32, scratch=scr)
     ynorm = float(torch.linalg.vector_norm(Yx[:, :k].double()))
     out = {"graph_edges": info.n_edges, "degree": ell, "k": k, "dtype": "f32"}
     seed = [SEED]
-    for B in batches:
-        def est():
-            seed[0] += 1
-            sped.apply_poly(G, V, Y, k, chain_dtype=torch.float32, mode=mode, walkers=B,
-                            seed=seed[0], scratch=scr)
-        est()
-        torch.cuda.synchronize()
-        err = float(torch.linalg.vector_norm((Y[:, :k] - Yx[:, :k]).double())) / ynorm
-        ms = _timed(torch, stream, est, reps)
-        out[f"batch_{B}"] = {"ms": ms, "edges_per_s": ell * B / (ms * 1e-3),
-                             "batch_over_edges": B / info.n_edges,
-                             "relative_error_vs_exact": err}
+    for md, tag in ((mode, "batch"), (sped.STOCHASTIC_MINIBATCH_STRATIFIED, "stratified_batch")):
+        for B in batches:
+            def est():
+                seed[0] += 1
+                sped.apply_poly(G, V, Y, k, chain_dtype=torch.float32, mode=md, walkers=B,
+                                seed=seed[0], scratch=scr)
+            est()
+            torch.cuda.synchronize()
+            err = float(torch.linalg.vector_norm((Y[:, :k] - Yx[:, :k]).double())) / ynorm
+            ms = _timed(torch, stream, est, reps)
+            out[f"{tag}_{B}"] = {"ms": ms, "edges_per_s": ell * B / (ms * 1e-3),
+                                 "batch_over_edges": B / info.n_edges,
+                                 "relative_error_vs_exact": err}
     # the two launches of one step, timed apart
     B = 1 << 20
     a, b, wv = sped.sample_edges(G, SEED, 0, B)
@@ -539,12 +544,16 @@ def measure_minibatch(sped, torch, g, G, dev, stream, k, ell, reps=5,
     Bs = Gs.info().n_edges // 4
     V0 = torch.from_numpy(gen.gaussian_block(n, ks, seed=SEED + 43)).to(dev)
     sb = {"graph": "sbm_n2000_b4_k4", "batch": Bs, "edges": Gs.info().n_edges}
-    for name, poly, eta in (("plain_mu_eg", ("shift", 1), None),
-                            ("limit7_mu_eg", ("limit", 7), 0.5)):
+    for name, poly, eta, md in (("plain_mu_eg", ("shift", 1), None, mode),
+                                ("limit7_mu_eg", ("limit", 7), 0.5, mode),
+                                ("plain_mu_eg_stratified", ("shift", 1), None,
+                                 sped.STOCHASTIC_MINIBATCH_STRATIFIED),
+                                ("limit7_mu_eg_stratified", ("limit", 7), 0.5,
+                                 sped.STOCHASTIC_MINIBATCH_STRATIFIED)):
         inf = (Gs.set_polynomial(sped.POLY_LIMIT_EXP, 7) if poly[0] == "limit"
                else Gs.set_polynomial(sped.POLY_SHIFT, 1))
         e = eta if eta is not None else 2.0 / inf.lambda_star
-        opts = sped.step_opts(sped.MU_EG, e, torch.float64, torch.float64, mode=mode, walkers=Bs,
+        opts = sped.step_opts(sped.MU_EG, e, torch.float64, torch.float64, mode=md, walkers=Bs,
                               seed=SEED)
         scr = torch.empty(sped.eig_step_scratch_bytes(Gs, opts, ks), dtype=torch.uint8,
                           device=dev)

@@ -66,7 +66,8 @@ typedef enum {
     SPED_EXACT = 0,               /* chained SpMM                                           */
     SPED_STOCHASTIC_IS = 1,       /* random-walk estimate, importance weights (Section 4.3) */
     SPED_STOCHASTIC_REJECT = 2,   /* random-walk estimate, the text's rejection step        */
-    SPED_STOCHASTIC_MINIBATCH = 3 /* every multiplication by L from its own edge minibatch  */
+    SPED_STOCHASTIC_MINIBATCH = 3, /* every multiplication by L from its own edge minibatch */
+    SPED_STOCHASTIC_MINIBATCH_STRATIFIED = 4 /* the same, one draw per stratum of the edges */
 } sped_mode;
 
 typedef enum { SPED_SOLVER_MU_EG = 0, SPED_SOLVER_OJA = 1 } sped_solver;
@@ -201,6 +202,11 @@ sped_status sped_set_schedule(sped_graph *g, int split, int merge_ipg);
  *    M V for every family. chain_t, v_t and y_t: F32 or F64 (the edge terms are added by
  *    atomic adds, so the summation order is not fixed: results match a sequential sum to
  *    rounding, not bit for bit). 1 <= B <= 2^32.
+ *  mode SPED_STOCHASTIC_MINIBATCH_STRATIFIED: variance reduction (left to future work in
+ *    Section 6). The edge ids are cut into B contiguous strata S_j = [floor(j |E| / B),
+ *    floor((j+1) |E| / B)); draw j is uniform in S_j (the first Lemire bounded draw over |S_j|
+ *    of the same stream) and L_hat_t = sum_j |S_j| w_{e_j} x_{e_j} x_{e_j}^T (empty strata, when
+ *    B > |E|, add nothing). Unbiased; B >= |E| gives L exactly.
  * ------------------------------------------------------------------------------------ */
 sped_status sped_apply_poly(const sped_graph *g, int k, const void *d_V, sped_dtype v_t, int ldv,
                             void *d_Y, sped_dtype y_t, int ldy, sped_dtype chain_t,
@@ -213,10 +219,12 @@ sped_status sped_apply_poly_scratch_size(const sped_graph *g, int k, sped_dtype 
 /* ------------------------------------------------------------------------------------
  * Edge minibatches fed from outside (Sections 2 and 6: edges arrive in minibatches, or are
  * drawn from a distribution such as a link-prediction model's output).
- * sped_sample_edges writes the minibatch that SPED_STOCHASTIC_MINIBATCH uses for
- * multiplication `step`: for draw j < count, d_a[j] < d_b[j] are the edge's endpoints and
- * d_w[j] its weight (1 for an unweighted graph); any output may be NULL. count <= 2^32, and the
- * graph must have an edge when count > 0.
+ * sped_sample_edges writes the minibatch that SPED_STOCHASTIC_MINIBATCH (stratified == 0) or
+ * SPED_STOCHASTIC_MINIBATCH_STRATIFIED (stratified != 0) uses for multiplication `step`: for
+ * draw j < count, d_a[j] < d_b[j] are the edge's endpoints and d_w[j] its weight (1 for an
+ * unweighted graph); with stratified draws d_size[j] = |S_j| (an empty stratum gives
+ * a = b = -1, w = 0, size 0; d_size is not written for uniform draws). Any output may be NULL.
+ * count <= 2^32, and the graph must have an edge when count > 0.
  * sped_edge_step runs one chain step on a caller-supplied minibatch:
  *   Y = alpha V + gamma X + beta * edge_scale * sum_{j<count} w_j x_j x_j^T X,
  * x_j = e_{a_j} - e_{b_j}; that is Y[a_j] += c_j (X[a_j] - X[b_j]) and Y[b_j] -= c_j (X[a_j] -
@@ -227,7 +235,8 @@ sped_status sped_apply_poly_scratch_size(const sped_graph *g, int k, sped_dtype 
  * may be NULL). The edge terms are added by atomic adds (order not fixed).
  * ------------------------------------------------------------------------------------ */
 sped_status sped_sample_edges(const sped_graph *g, uint64_t seed, uint32_t step, int64_t count,
-                              int32_t *d_a, int32_t *d_b, float *d_w, void *stream);
+                              int stratified, int32_t *d_a, int32_t *d_b, float *d_w,
+                              int32_t *d_size, void *stream);
 
 sped_status sped_edge_step(int64_t n, int k, const int32_t *d_a, const int32_t *d_b,
                            const float *d_w, int64_t count, double edge_scale, const void *d_X,

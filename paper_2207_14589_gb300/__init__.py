@@ -21,7 +21,8 @@ OK, ERR_INVALID_ARG, ERR_BAD_CSR, ERR_UNSUPPORTED, ERR_NUMERIC, ERR_NOT_CONVERGE
     ERR_TIMEOUT, ERR_CUDA, ERR_SCRATCH = range(9)
 BF16, F32, F64 = 0, 1, 2
 POLY_LIMIT_EXP, POLY_TAYLOR_EXP, POLY_TAYLOR_LOG, POLY_MONOMIAL, POLY_SHIFT, POLY_CHEBYSHEV = range(6)
-EXACT, STOCHASTIC_IS, STOCHASTIC_REJECT, STOCHASTIC_MINIBATCH = range(4)
+(EXACT, STOCHASTIC_IS, STOCHASTIC_REJECT, STOCHASTIC_MINIBATCH,
+ STOCHASTIC_MINIBATCH_STRATIFIED) = range(5)
 MU_EG, OJA = 0, 1
 
 _STATUS = {0: "OK", 1: "INVALID_ARG", 2: "BAD_CSR", 3: "UNSUPPORTED", 4: "NUMERIC",
@@ -117,7 +118,7 @@ def lib():
         "sped_autotune_scratch_size": [vp, i32, i32, P(sz)],
         "sped_autotune": [vp, i32, i32, vp, sz, vp, P(sped_tune_report)],
         "sped_set_schedule": [vp, i32, i32],
-        "sped_sample_edges": [vp, u64, ctypes.c_uint32, i64, vp, vp, vp, vp],
+        "sped_sample_edges": [vp, u64, ctypes.c_uint32, i64, i32, vp, vp, vp, vp, vp],
         "sped_edge_step": [i64, i32, vp, vp, vp, i64, dbl, vp, i32, i32, vp, i32, i32, vp, i32,
                            i32, dbl, dbl, dbl, vp, vp],
     }
@@ -322,15 +323,19 @@ def apply_poly(g: Graph, V, Y, k, chain_dtype=None, mode=EXACT, walkers=0, seed=
     return Y
 
 
-def sample_edges(g: Graph, seed, step, count, stream=None):
-    """The edge minibatch that STOCHASTIC_MINIBATCH draws for multiplication `step`:
-    (a, b, w) device tensors (int32, int32, float32) of length count, a < b."""
+def sample_edges(g: Graph, seed, step, count, stratified=False, stream=None):
+    """The edge minibatch that STOCHASTIC_MINIBATCH (or, stratified, STOCHASTIC_MINIBATCH_
+    STRATIFIED) draws for multiplication `step`: (a, b, w) device tensors (int32, int32,
+    float32) of length count, a < b; stratified draws add the stratum sizes (int32)."""
     dev = torch.device("cuda", torch.cuda.current_device())
     a = torch.empty(max(int(count), 1), dtype=torch.int32, device=dev)
     b = torch.empty_like(a)
     w = torch.empty(max(int(count), 1), dtype=torch.float32, device=dev)
-    _check(lib().sped_sample_edges(g.handle, int(seed), int(step), int(count), _ptr(a), _ptr(b),
-                                   _ptr(w), _stream(stream)))
+    size = torch.empty_like(a) if stratified else None
+    _check(lib().sped_sample_edges(g.handle, int(seed), int(step), int(count), int(stratified),
+                                   _ptr(a), _ptr(b), _ptr(w), _ptr(size), _stream(stream)))
+    if stratified:
+        return a[:count], b[:count], w[:count], size[:count]
     return a[:count], b[:count], w[:count]
 
 

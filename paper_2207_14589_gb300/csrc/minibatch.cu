@@ -14,6 +14,13 @@
 // Draws: draw j of multiplication t is the first Lemire bounded draw in [0, |E|) of the word
 // stream (seed; counter words j, t, 0x4D42), so every draw is independent of the others and of
 // the batch size; edges are numbered by the CSR order of their upper entries.
+//
+// Stratified minibatches (variance reduction, left to future work in Section 6): the edge ids
+// are cut into B contiguous strata S_j = [floor(j|E|/B), floor((j+1)|E|/B)), draw j is uniform
+// in S_j (the same stream, range |S_j|) and stands for its stratum with weight |S_j|, so
+// L_hat = sum_j |S_j| w_j x_j x_j^T is unbiased. The strata follow the CSR order, so a
+// minibatch covers every part of the graph in proportion, and consecutive draws touch nearby
+// rows.
 #include "sped_internal.cuh"
 
 namespace sped {
@@ -21,13 +28,31 @@ namespace sped {
 constexpr uint32_t MB_TAG = 0x4D42u;
 constexpr int MB_THREADS = 256;
 
+// Draw j of a minibatch of `count`: uniform over the edges, or (STRAT) uniform in stratum j
+// with size = |S_j|; an empty stratum gives a = b = -1, size 0.
+template <bool STRAT>
 __device__ __forceinline__ void draw_edge(uint64_t seed, uint32_t step, uint32_t j,
-                                          uint32_t n_edges, const int2 *__restrict__ edge_ab,
+                                          uint32_t n_edges, uint64_t count,
+                                          const int2 *__restrict__ edge_ab,
                                           const int32_t *__restrict__ edge_p,
                                           const float *__restrict__ w, int32_t &a, int32_t &b,
-                                          float &wv) {
+                                          float &wv, int32_t &size) {
     WordStream s(seed, j, step, MB_TAG);
-    const uint32_t e = s.bounded(n_edges);
+    uint32_t e;
+    if constexpr (STRAT) {
+        const uint64_t lo = (uint64_t)j * n_edges / count;
+        const uint64_t hi = ((uint64_t)j + 1) * n_edges / count;
+        size = (int32_t)(hi - lo);
+        if (size == 0) {
+            a = b = -1;
+            wv = 0.f;
+            return;
+        }
+        e = (uint32_t)lo + s.bounded((uint32_t)size);
+    } else {
+        size = 1;
+        e = s.bounded(n_edges);
+    }
     const int2 ab = __ldg(edge_ab + e);
     a = ab.x;
     b = ab.y;
@@ -37,20 +62,23 @@ __device__ __forceinline__ void draw_edge(uint64_t seed, uint32_t step, uint32_t
 // ---------------------------------------------------------------------------------------
 // the sampled edges themselves
 // ---------------------------------------------------------------------------------------
+template <bool STRAT>
 __global__ void __launch_bounds__(MB_THREADS)
     k_sample_edges(int64_t count, uint64_t seed, uint32_t step, uint32_t n_edges,
                    const int2 *__restrict__ edge_ab, const int32_t *__restrict__ edge_p,
-                   const float *__restrict__ w,
-                   int32_t *__restrict__ out_a, int32_t *__restrict__ out_b,
-                   float *__restrict__ out_w) {
+                   const float *__restrict__ w, int32_t *__restrict__ out_a,
+                   int32_t *__restrict__ out_b, float *__restrict__ out_w,
+                   int32_t *__restrict__ out_size) {
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < count;
          j += (int64_t)gridDim.x * blockDim.x) {
-        int32_t a, b;
+        int32_t a, b, size;
         float wv;
-        draw_edge(seed, step, (uint32_t)j, n_edges, edge_ab, edge_p, w, a, b, wv);
+        draw_edge<STRAT>(seed, step, (uint32_t)j, n_edges, (uint64_t)count, edge_ab, edge_p, w,
+                         a, b, wv, size);
         if (out_a) out_a[j] = a;
         if (out_b) out_b[j] = b;
         if (out_w) out_w[j] = wv;
+        if (STRAT && out_size) out_size[j] = size;
     }
 }
 
@@ -155,7 +183,8 @@ __device__ __forceinline__ void chunk_atomic_add(double *p, const double *d, dou
     atomicAdd(p + 1, sgn * d[1]);
 }
 
-template <typename TX, typename TY, bool DRAW>
+// SRC: 0 = the caller's edge arrays, 1 = uniform draws, 2 = stratified draws
+template <typename TX, typename TY, int SRC>
 __global__ void __launch_bounds__(MB_THREADS)
     k_edge_scatter(int64_t n, int k, int lanes_log2, const TX *__restrict__ X, int ldx, TY *Y,
                    int ldy, int64_t count, double coef, uint64_t seed, uint32_t step,
@@ -176,11 +205,12 @@ __global__ void __launch_bounds__(MB_THREADS)
     // through the shuffles below
     for (int64_t wbase = warp_group0 * C; wbase < count; wbase += n_groups * C) {
         const int64_t j = wbase + (group - warp_group0) * C + sub;
-        int32_t a = -1, b = -1;
+        int32_t a = -1, b = -1, size = 0;
         float wv = 0.f;
         if (j < count) {
-            if constexpr (DRAW) {
-                draw_edge(seed, step, (uint32_t)j, n_edges, edge_ab, edge_p, w, a, b, wv);
+            if constexpr (SRC != 0) {
+                draw_edge<SRC == 2>(seed, step, (uint32_t)j, n_edges, (uint64_t)count, edge_ab,
+                                    edge_p, w, a, b, wv, size);
             } else {
                 a = __ldg(ea + j);
                 b = __ldg(eb + j);
@@ -196,7 +226,13 @@ __global__ void __launch_bounds__(MB_THREADS)
             const int32_t qb = __shfl_sync(0xffffffffu, b, q, C);
             const float qw = __shfl_sync(0xffffffffu, wv, q, C);
             if (qa < 0) continue;
-            const A cq = (A)(coef * (double)qw);
+            A cq;
+            if constexpr (SRC == 2) {
+                const int32_t qs = __shfl_sync(0xffffffffu, size, q, C);
+                cq = (A)(coef * (double)qw * (double)qs);
+            } else {
+                cq = (A)(coef * (double)qw);
+            }
             const TX *xa = X + (int64_t)qa * ldx;
             const TX *xb = X + (int64_t)qb * ldx;
             TY *ya = Y + (int64_t)qa * ldy;
@@ -269,11 +305,16 @@ static sped_status run_scatter(int64_t n, int k, const void *X, int ldx, void *Y
     const int grid = grid_for(groups_needed, l2);
     if (eb.graph) {
         const sped_graph *g = eb.graph;
-        k_edge_scatter<TX, TY, true><<<grid, MB_THREADS, 0, st>>>(
-            n, k, l2, (const TX *)X, ldx, (TY *)Y, ldy, eb.count, coef, eb.seed, eb.step,
-            (uint32_t)g->n_edges, g->edge_ab, g->edge_p, nullptr, nullptr, g->w, nullptr);
+        if (eb.stratified)
+            k_edge_scatter<TX, TY, 2><<<grid, MB_THREADS, 0, st>>>(
+                n, k, l2, (const TX *)X, ldx, (TY *)Y, ldy, eb.count, coef, eb.seed, eb.step,
+                (uint32_t)g->n_edges, g->edge_ab, g->edge_p, nullptr, nullptr, g->w, nullptr);
+        else
+            k_edge_scatter<TX, TY, 1><<<grid, MB_THREADS, 0, st>>>(
+                n, k, l2, (const TX *)X, ldx, (TY *)Y, ldy, eb.count, coef, eb.seed, eb.step,
+                (uint32_t)g->n_edges, g->edge_ab, g->edge_p, nullptr, nullptr, g->w, nullptr);
     } else {
-        k_edge_scatter<TX, TY, false><<<grid, MB_THREADS, 0, st>>>(
+        k_edge_scatter<TX, TY, 0><<<grid, MB_THREADS, 0, st>>>(
             n, k, l2, (const TX *)X, ldx, (TY *)Y, ldy, eb.count, coef, 0, 0, 0, nullptr, nullptr,
             eb.a, eb.b, eb.w, eb.skipped);
     }
@@ -325,17 +366,24 @@ using namespace sped;
 extern "C" {
 
 sped_status sped_sample_edges(const sped_graph *g, uint64_t seed, uint32_t step, int64_t count,
-                              int32_t *d_a, int32_t *d_b, float *d_w, void *stream) {
+                              int stratified, int32_t *d_a, int32_t *d_b, float *d_w,
+                              int32_t *d_size, void *stream) {
     if (!g) return fail(SPED_ERR_INVALID_ARG, "sample_edges: null graph");
     if (count < 0 || count > (int64_t)UINT32_MAX + 1)
         return fail(SPED_ERR_INVALID_ARG, "sample_edges: count %lld not in 0..2^32",
                     (long long)count);
     if (count > 0 && g->n_edges < 1)
         return fail(SPED_ERR_INVALID_ARG, "sample_edges: the graph has no edges");
-    if (count == 0 || (!d_a && !d_b && !d_w)) return SPED_OK;
+    if (count == 0 || (!d_a && !d_b && !d_w && !d_size)) return SPED_OK;
     const int grid = grid_for(count, 0);
-    k_sample_edges<<<grid, MB_THREADS, 0, as_stream(stream)>>>(
-        count, seed, step, (uint32_t)g->n_edges, g->edge_ab, g->edge_p, g->w, d_a, d_b, d_w);
+    if (stratified)
+        k_sample_edges<true><<<grid, MB_THREADS, 0, as_stream(stream)>>>(
+            count, seed, step, (uint32_t)g->n_edges, g->edge_ab, g->edge_p, g->w, d_a, d_b, d_w,
+            d_size);
+    else
+        k_sample_edges<false><<<grid, MB_THREADS, 0, as_stream(stream)>>>(
+            count, seed, step, (uint32_t)g->n_edges, g->edge_ab, g->edge_p, g->w, d_a, d_b, d_w,
+            nullptr);
     SPED_CHECK_LAUNCH("k_sample_edges");
     return SPED_OK;
 }

@@ -318,7 +318,8 @@ struct EdgeBatch {
     uint64_t seed = 0;
     uint32_t step = 0;
     int64_t count = 0;
-    double scale = 1.0;  // |E| / count for uniform draws
+    double scale = 1.0;  // |E| / count for uniform draws, 1 for stratified draws
+    bool stratified = false;  // one draw per stratum of the edge order, weight |S_j|
     const int32_t *a = nullptr, *b = nullptr;
     const float *w = nullptr;
     int32_t *skipped = nullptr;

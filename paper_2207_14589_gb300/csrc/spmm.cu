@@ -548,12 +548,14 @@ static int chain_buffers(const std::vector<StepCoef> &cs) {
 }
 
 size_t apply_poly_scratch(const sped_graph *g, int k, sped_dtype ct, sped_mode mode) {
-    if (mode != SPED_EXACT && mode != SPED_STOCHASTIC_MINIBATCH) return 0;
+    if (mode != SPED_EXACT && mode != SPED_STOCHASTIC_MINIBATCH &&
+        mode != SPED_STOCHASTIC_MINIBATCH_STRATIFIED)
+        return 0;
     const int nbuf = chain_buffers(chain_coefs(g->poly));
     ScratchPlan p;
     size_t buf = (size_t)g->n * padded_ld(k, ct) * dtype_size(ct);
     for (int i = 0; i < nbuf; ++i) p.add(buf);
-    if (mode == SPED_STOCHASTIC_MINIBATCH) return p.total();
+    if (mode != SPED_EXACT) return p.total();
     size_t ms = 0;
     for (sped_dtype t : {SPED_BF16, SPED_F32, SPED_F64}) {
         size_t x = poly_step_scratch(g, k, t, 0);
@@ -569,7 +571,8 @@ sped_status apply_poly_impl(const sped_graph *g, int k, const void *V, sped_dtyp
                             const void *X0, sped_dtype x0t, int ldx0) {
     if (mode == SPED_STOCHASTIC_IS || mode == SPED_STOCHASTIC_REJECT)
         return launch_walk(g, k, V, vt, ldv, Y, yt, ldy, mode, walkers, seed, st);
-    const bool minibatch = mode == SPED_STOCHASTIC_MINIBATCH;
+    const bool stratified = mode == SPED_STOCHASTIC_MINIBATCH_STRATIFIED;
+    const bool minibatch = mode == SPED_STOCHASTIC_MINIBATCH || stratified;
     if (mode != SPED_EXACT && !minibatch)
         return fail(SPED_ERR_INVALID_ARG, "apply_poly: mode %d", (int)mode);
     if (minibatch) {
@@ -614,7 +617,8 @@ sped_status apply_poly_impl(const sped_graph *g, int k, const void *V, sped_dtyp
             eb.seed = seed;
             eb.step = (uint32_t)t;
             eb.count = g->n_edges > 0 ? walkers : 0;
-            eb.scale = (double)g->n_edges / (double)walkers;
+            eb.scale = stratified ? 1.0 : (double)g->n_edges / (double)walkers;
+            eb.stratified = stratified;
             SPED_TRY(launch_edge_step(g->n, k, x, xt, ldx, cs[t].uses_v ? V : nullptr, vt, ldv,
                                       w2, ldc, cs[t].delta, y, ytt, ldyy, cs[t].alpha,
                                       cs[t].beta, cs[t].gamma, eb, st));
@@ -674,7 +678,7 @@ sped_status sped_apply_poly(const sped_graph *g, int k, const void *d_V, sped_dt
     SPED_TRY(check_layout(d_Y, y_t, k, ldy, "apply_poly Y"));
     if (!dtype_valid(chain_t)) return fail(SPED_ERR_INVALID_ARG, "apply_poly: chain dtype");
     if (mode != SPED_EXACT && mode != SPED_STOCHASTIC_IS && mode != SPED_STOCHASTIC_REJECT &&
-        mode != SPED_STOCHASTIC_MINIBATCH)
+        mode != SPED_STOCHASTIC_MINIBATCH && mode != SPED_STOCHASTIC_MINIBATCH_STRATIFIED)
         return fail(SPED_ERR_INVALID_ARG, "apply_poly: mode %d", (int)mode);
     if (d_V == d_Y) return fail(SPED_ERR_INVALID_ARG, "apply_poly: V and Y must not alias");
     Scratch scr(d_scratch, scratch_bytes);

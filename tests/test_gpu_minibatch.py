@@ -198,3 +198,81 @@ def test_minibatch_rejects_what_it_cannot_do():
     with pytest.raises(sped.SpedError):
         sped.edge_step(g.n, V, V, 4, torch.zeros(1, dtype=torch.int32, device=DEV),
                        torch.zeros(1, dtype=torch.int32, device=DEV))
+
+
+# ---- stratified minibatches ------------------------------------------------------------
+@pytest.mark.parametrize("count", [1, 1000, 4097, 20000])
+def test_stratified_edges_match_oracle(count):
+    g = _weighted()
+    G = sped.Graph.from_csr(g)
+    a, b, w, size = sped.sample_edges(G, seed=77, step=3, count=count, stratified=True)
+    torch.cuda.synchronize()
+    ea, eb, ew = oracle.edge_list(g)
+    ids, sizes = oracle.stratified_edge_ids(len(ea), 77, 3, count)
+    assert np.array_equal(size.cpu().numpy(), sizes)
+    keep = sizes > 0  # count > |E| leaves empty strata: a = b = -1, w = 0
+    assert np.array_equal(a.cpu().numpy()[keep], ea[ids[keep]])
+    assert np.array_equal(b.cpu().numpy()[keep], eb[ids[keep]])
+    assert np.array_equal(w.cpu().numpy()[keep].astype(np.float64), ew[ids[keep]])
+    assert np.all(a.cpu().numpy()[~keep] == -1) and np.all(w.cpu().numpy()[~keep] == 0)
+
+
+@pytest.mark.parametrize("fam,ell", [("limit", 3), ("limit", 9), ("taylor_exp", 4),
+                                     ("chebyshev", 5)])
+@pytest.mark.parametrize("ct", [torch.float64, torch.float32])
+@pytest.mark.parametrize("B", [1, 97, 5000])
+def test_stratified_chain_same_draws_as_oracle(fam, ell, ct, B):
+    g = _weighted()
+    G = sped.Graph.from_csr(g)
+    chain = _family(G, g, fam, ell)
+    k = 6
+    V0 = gen.gaussian_block(g.n, k, seed=46)
+    V = to_block(V0, ct)
+    Y = sped.alloc_block(g.n, k, ct, DEV)
+    seed = 7654321 + B
+    sped.apply_poly(G, V, Y, k, chain_dtype=ct, mode=sped.STOCHASTIC_MINIBATCH_STRATIFIED,
+                    walkers=B, seed=seed)
+    torch.cuda.synchronize()
+    want = chain(stored(V0, ct), oracle.minibatch_operator(g, seed, B, stratified=True))
+    tol = 1e-11 if ct == torch.float64 else 2e-5 * max(1, ell)
+    assert rel(host(Y, k), want) <= tol
+
+
+def test_stratified_with_one_edge_per_stratum_is_exact():
+    g = _weighted()
+    G = sped.Graph.from_csr(g)
+    info = G.set_polynomial(sped.POLY_LIMIT_EXP, 5)
+    k = 4
+    V0 = gen.gaussian_block(g.n, k, seed=47)
+    V = to_block(V0, torch.float64)
+    Y = sped.alloc_block(g.n, k, torch.float64, DEV)
+    for B in (info.n_edges, info.n_edges + 31):
+        sped.apply_poly(G, V, Y, k, chain_dtype=torch.float64,
+                        mode=sped.STOCHASTIC_MINIBATCH_STRATIFIED, walkers=B, seed=5)
+        torch.cuda.synchronize()
+        assert rel(host(Y, k), oracle.poly_limit(g, V0, info.scale_s, 5)) <= 1e-12
+
+
+def test_stratified_mean_converges_and_beats_uniform():
+    g = gen.sbm(600, 3, 0.05, 0.004, seed=37)
+    G = sped.Graph.from_csr(g)
+    ell, k, R = 5, 2, 300
+    info = G.set_polynomial(sped.POLY_LIMIT_EXP, ell)
+    V0 = gen.gaussian_block(g.n, k, seed=38)
+    V = to_block(V0, torch.float64)
+    Y = sped.alloc_block(g.n, k, torch.float64, DEV)
+    exact = oracle.poly_limit(g, V0, info.scale_s, ell)
+    spread = {}
+    for mode in (sped.STOCHASTIC_MINIBATCH, sped.STOCHASTIC_MINIBATCH_STRATIFIED):
+        outs = []
+        for r in range(R):
+            sped.apply_poly(G, V, Y, k, chain_dtype=torch.float64, mode=mode, walkers=2000,
+                            seed=r)
+            outs.append(host(Y, k))
+        outs = np.stack(outs)
+        mean, se = outs.mean(0), outs.std(0, ddof=1) / np.sqrt(R)
+        z = (mean - exact) / np.maximum(se, 1e-300)
+        assert float(np.mean(z ** 2)) < 1.4
+        assert float(np.abs(z).max()) < 6.0
+        spread[mode] = float(np.mean(np.linalg.norm(outs - exact, axis=(1, 2))))
+    assert spread[sped.STOCHASTIC_MINIBATCH_STRATIFIED] < spread[sped.STOCHASTIC_MINIBATCH]
