@@ -489,20 +489,6 @@ def measure_minibatch(sped, torch, g, G, dev, stream, k, ell, reps=5,
     sped.apply_poly(G, V, Yx, k, chain_dtype=torch.float32, scratch=scr)
     ynorm = float(torch.linalg.vector_norm(Yx[:, :k].double()))
     out = {"graph_edges": info.n_edges, "degree": ell, "k": k, "dtype": "f32"}
-    seed = [SEED]
-    for md, tag in ((mode, "batch"), (sped.STOCHASTIC_MINIBATCH_STRATIFIED, "stratified_batch")):
-        for B in batches:
-            def est():
-                seed[0] += 1
-                sped.apply_poly(G, V, Y, k, chain_dtype=torch.float32, mode=md, walkers=B,
-                                seed=seed[0], scratch=scr)
-            est()
-            torch.cuda.synchronize()
-            err = float(torch.linalg.vector_norm((Y[:, :k] - Yx[:, :k]).double())) / ynorm
-            ms = _timed(torch, stream, est, reps)
-            out[f"{tag}_{B}"] = {"ms": ms, "edges_per_s": ell * B / (ms * 1e-3),
-                                 "batch_over_edges": B / info.n_edges,
-                                 "relative_error_vs_exact": err}
     # the two launches of one step, timed apart
     B = 1 << 20
     a, b, wv = sped.sample_edges(G, SEED, 0, B)
@@ -522,13 +508,31 @@ def measure_minibatch(sped, torch, g, G, dev, stream, k, ell, reps=5,
     ms_one = _timed(torch, stream, one, 20)
     per_draw = 12 + 2 * k * 4 + 2 * 2 * k * 4
     scatter_ms = max(ms_f - ms_d, 1e-6)
+    peak, peak_src = _peaks()
     out["step_b1048576"] = {
         "dense_ms": ms_d, "dense_gbs": 2 * g.n * k * 4 / (ms_d * 1e-3) / 1e9,
+        "dense_frac": 2 * g.n * k * 4 / (ms_d * 1e-3) / 1e9 / peak,
+        "peak_gbs": peak, "peak_source": peak_src,
         "scatter_ms": scatter_ms, "scatter_bytes_per_draw": per_draw,
         "scatter_gbs": B * per_draw / (scatter_ms * 1e-3) / 1e9,
         "draws_per_s": B / (scatter_ms * 1e-3),
         "chain_step_drawn_ms": ms_one,
         "drawn_scatter_ms": max(ms_one - ms_d, 1e-6)}
+    G.set_polynomial(sped.POLY_LIMIT_EXP, ell)
+    seed = [SEED]
+    for md, tag in ((mode, "batch"), (sped.STOCHASTIC_MINIBATCH_STRATIFIED, "stratified_batch")):
+        for B in batches:
+            def est():
+                seed[0] += 1
+                sped.apply_poly(G, V, Y, k, chain_dtype=torch.float32, mode=md, walkers=B,
+                                seed=seed[0], scratch=scr)
+            est()
+            torch.cuda.synchronize()
+            err = float(torch.linalg.vector_norm((Y[:, :k] - Yx[:, :k]).double())) / ynorm
+            ms = _timed(torch, stream, est, reps)
+            out[f"{tag}_{B}"] = {"ms": ms, "edges_per_s": ell * B / (ms * 1e-3),
+                                 "batch_over_edges": B / info.n_edges,
+                                 "relative_error_vs_exact": err}
     del scr, V, Y, Yx
     # stochastic mu-EG on the small SBM
     gs = gen.sbm(2000, 4, 0.05, 0.001, seed=SEED)
@@ -906,15 +910,21 @@ def run_ours(args, rank, world, local_rank):
 
     extra = {}
     if rank == 0 and not args.no_extra:
+        want = set(args.only_extra.split(",")) if args.only_extra else None
+        runs = {
+            "stochastic": lambda: measure_stochastic(sped, torch, g, G, dev, stream, k, ell),
+            "minibatch": lambda: measure_minibatch(sped, torch, g, G, dev, stream, k, ell),
+            "differentiable": lambda: measure_differentiable(sped, torch, dev, stream),
+            "batched": lambda: measure_batched(sped, torch, dev, stream,
+                                               n_graphs=args.batched_graphs),
+            "permuted_node_order": lambda: measure_permuted(sped, torch, dev, stream, k, ell),
+            "degree_sweep": lambda: measure_degree_sweep(sped, torch, dev, stream),
+            "three_room": lambda: measure_three_room(sped, torch, dev, stream)}
         # gathered bytes of one chain step (every stored entry pulls one k-column row)
         extra["gather_bytes_per_launch"] = g.nnz * k * 2
-        extra["stochastic"] = measure_stochastic(sped, torch, g, G, dev, stream, k, ell)
-        extra["minibatch"] = measure_minibatch(sped, torch, g, G, dev, stream, k, ell)
-        extra["differentiable"] = measure_differentiable(sped, torch, dev, stream)
-        extra["batched"] = measure_batched(sped, torch, dev, stream, n_graphs=args.batched_graphs)
-        extra["permuted_node_order"] = measure_permuted(sped, torch, dev, stream, k, ell)
-        extra["degree_sweep"] = measure_degree_sweep(sped, torch, dev, stream)
-        extra["three_room"] = measure_three_room(sped, torch, dev, stream)
+        for name, fn in runs.items():
+            if want is None or name in want:
+                extra[name] = fn()
     if rank == 0 and args.power_law:
         extra["power_law"] = measure_power_law(sped, torch, dev, stream, n=args.power_law_n,
                                                target_nnz=args.target_nnz)
@@ -962,6 +972,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the stochastic, differentiable and batched measurements")
+    ap.add_argument("--only-extra", default=None,
+                    help="comma list of the extra measurements to run (stochastic, minibatch, "
+                         "differentiable, batched, permuted_node_order, degree_sweep, "
+                         "three_room); default all")
     ap.add_argument("--batched-graphs", type=int, default=4096,
                     help="number of graphs of the batched measurement")
     ap.add_argument("--power-law", action="store_true",
