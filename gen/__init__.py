@@ -115,6 +115,22 @@ def cycle(n: int) -> CSRGraph:
     return from_edges(n, i, (i + 1) % n, name=f"cycle{n}")
 
 
+def cycle_csr(n: int) -> CSRGraph:
+    """The cycle C_n (n >= 3) built directly in CSR, O(n) memory and time (for sizes where the
+    sorting in from_edges would be slow): row r holds r - 1 and r + 1 modulo n, sorted."""
+    if n < 3:
+        raise ValueError("cycle needs n >= 3")
+    r = np.arange(n, dtype=np.int64)
+    lo = np.where(r == 0, 1, r - 1)
+    hi = np.where(r == 0, n - 1, np.where(r == n - 1, r - 1, r + 1))
+    lo[n - 1] = 0
+    col = np.empty(2 * n, dtype=np.int32)
+    col[0::2] = lo
+    col[1::2] = hi
+    row_ptr = (2 * np.arange(n + 1, dtype=np.int64)).astype(np.int32)
+    return CSRGraph(n=n, row_ptr=row_ptr, col_idx=col, name=f"cycle{n}")
+
+
 def complete(n: int) -> CSRGraph:
     a, b = np.triu_indices(n, 1)
     return from_edges(n, a, b, name=f"K{n}")
@@ -395,6 +411,23 @@ def three_room_grid(s: int = 2, h: int = 10) -> CSRGraph:
 def gaussian_block(n: int, k: int, seed: int = DEFAULT_SEED) -> np.ndarray:
     """V0 with i.i.d. N(0,1) entries (float64, row-major n x k)."""
     return np.random.default_rng(seed).standard_normal((n, k))
+
+
+def hash_block(rows, k: int, xp=np):
+    """Deterministic block for sizes beyond host memory: entry (r, c) = (h & 255) / 256 - 1/2
+    with h an integer hash of (r, c), so every value has at most 8 significant bits (exact in
+    BF16). `rows` is an integer array (numpy or torch, `xp` its module); the same values come
+    out on the host and on a device."""
+    r = rows.reshape(-1, 1).to(xp.int64) if xp is not np else np.asarray(rows, np.int64)[:, None]
+    c = xp.arange(k, dtype=xp.int64)
+    if xp is not np:
+        c = c.to(r.device)
+    m32 = 0xFFFFFFFF
+    h = (r * 0x9E3779B1 + c * 0x85EBCA77) & m32
+    h = h ^ (h >> 15)
+    h = (h * 0x2C1B3C6D) & m32
+    h = h ^ (h >> 12)
+    return (h & 255).to(xp.float64) / 256.0 - 0.5 if xp is not np else (h & 255) / 256.0 - 0.5
 
 
 def uniform_edge_weights(g: CSRGraph, lo: float = 0.5, hi: float = 1.5,
