@@ -255,6 +255,36 @@ def scale_rule(lam_bound, ell):
     return 1.0 / ell if ell >= lam_bound / 2.0 else 2.0 / lam_bound
 
 
+def poly_moments(g, V, n_moments, basis="chebyshev", a=0.0, b=1.0):
+    """Block moments Omega_l = V^T B_l V (k x k), l = 0..n_moments-1, of the power basis
+    B_l = L^l or the Chebyshev basis B_l = T_l(x), x = (2L - (a + b) I) / (b - a) (three-term
+    recurrence). For M = sum_l c_l B_l they give V^T M V = sum_l c_l Omega_l, the quantity a fit
+    of the coefficients (the meta-learning the paper leaves to future work, Section 6) works
+    on."""
+    V = np.asarray(V, dtype=np.float64)
+    out = []
+    if basis == "power":
+        X = V
+        for _ in range(n_moments):
+            out.append(V.T @ X)
+            X = laplacian_apply(g, X)
+        return np.stack(out)
+    al, be = 2.0 / (b - a), -(a + b) / (b - a)
+    T0, T1 = V, None
+    for l in range(n_moments):
+        if l == 0:
+            T = V
+        elif l == 1:
+            T1 = al * laplacian_apply(g, V) + be * V
+            T = T1
+        else:
+            T2 = 2.0 * (al * laplacian_apply(g, T1) + be * T1) - T0
+            T0, T1 = T1, T2
+            T = T2
+        out.append(V.T @ T)
+    return np.stack(out)
+
+
 # ----------------------------------------------------------------------------------------
 # Section 4.3: stochastic estimate over sampled walks
 # ----------------------------------------------------------------------------------------

@@ -142,3 +142,43 @@ def test_chebyshev_product_identity():
         rhs = 0.5 * (oracle.poly_chebyshev(g, V, e(m + k), a, b) +
                      oracle.poly_chebyshev(g, V, e(abs(m - k)), a, b))
         assert np.allclose(lhs, rhs, rtol=1e-10, atol=1e-10 * np.abs(rhs).max())
+
+
+# ---- block moments of the polynomial bases (for fitting coefficients) --------------------
+def test_moments_on_closed_form_eigenpairs():
+    # V = eigenvectors: Omega_l = diag(lambda^l) (power) and diag(T_l(x(lambda))) (Chebyshev)
+    n = 24
+    g = gen.path(n)
+    lam, U = _path_pairs(n)
+    idx = [0, 3, 7, 20]
+    V = U[:, idx]
+    P = oracle.poly_moments(g, V, 6, basis="power")
+    for l in range(6):
+        assert np.allclose(P[l], np.diag(lam[idx] ** l), atol=1e-11 * max(1, 4.0 ** l))
+    a, b = 0.1, 4.0
+    C = oracle.poly_moments(g, V, 9, basis="chebyshev", a=a, b=b)
+    x = (2 * lam[idx] - (a + b)) / (b - a)
+    for l in range(9):
+        e = np.zeros(l + 1)
+        e[l] = 1.0
+        assert np.allclose(C[l], np.diag(oracle.chebyshev_scalar(e, x)), atol=1e-11)
+
+
+def test_moments_product_identity_and_linearity():
+    # (T_l V)^T (T_m V) = (Omega_{l+m} + Omega_{|l-m|}) / 2, and sum_l c_l Omega_l = V^T M V
+    g = gen.uniform_edge_weights(gen.random_graph(80, 300, seed=3), seed=4)
+    V = gen.gaussian_block(g.n, 3, seed=5)
+    a, b = 0.0, oracle.gershgorin_bound(g)
+    C = oracle.poly_moments(g, V, 12, a=a, b=b)
+    for l, m in [(0, 0), (1, 4), (5, 5), (2, 7)]:
+        el, em = np.zeros(l + 1), np.zeros(m + 1)
+        el[l], em[m] = 1.0, 1.0
+        TlV = oracle.poly_chebyshev(g, V, el, a, b)
+        TmV = oracle.poly_chebyshev(g, V, em, a, b)
+        assert np.allclose(TlV.T @ TmV, 0.5 * (C[l + m] + C[abs(l - m)]), rtol=1e-10,
+                           atol=1e-10)
+    c = np.random.default_rng(6).standard_normal(8)
+    assert np.allclose(np.tensordot(c, C[:8], axes=1), V.T @ oracle.poly_chebyshev(g, V, c, a, b),
+                       rtol=1e-10, atol=1e-10)
+    P = oracle.poly_moments(g, V, 5, basis="power")
+    assert np.allclose(P[3], V.T @ oracle.walk_exact_terms(g, V, [0, 0, 0, 1.0]), rtol=1e-12)
