@@ -668,6 +668,87 @@ def measure_three_room(sped, torch, dev, stream, k=3, cap_plain=20000, cap_dilat
     return out
 
 
+def _fit_chebyshev(mu, d, k, a, b, c0):
+    """Coefficients c of M = sum_l c_l T_l(x) on [a, b] minimising the sum of the Ritz values of
+    L on span(M V), from the block moments mu_l = V^T T_l V (l <= 2d + 1): with Y = M V,
+    Y^T Y = sum c_l c_m (mu_{l+m} + mu_{|l-m|}) / 2 and Y^T L Y = sum c_l c_m V^T T_l L T_m V,
+    L = (b - a)/2 x + (a + b)/2 I, x T_m = (T_{m+1} + T_{|m-1|}) / 2. BFGS with the analytic
+    gradient of tr((Y^T Y)^-1 Y^T L Y); c is scale-free and returned with unit norm."""
+    import scipy.optimize as so
+    A = np.empty((d + 1, d + 1, k, k))
+    X = np.empty_like(A)
+    for l in range(d + 1):
+        for m in range(d + 1):
+            A[l, m] = 0.5 * (mu[l + m] + mu[abs(l - m)])
+            X[l, m] = 0.25 * (mu[l + m + 1] + mu[abs(l - m - 1)] + mu[l + abs(m - 1)]
+                              + mu[abs(l - abs(m - 1))])
+    Bm = 0.5 * (b - a) * X + 0.5 * (a + b) * A
+
+    def f(c):
+        S = np.einsum("l,m,lmij->ij", c, c, A)
+        Q = np.einsum("l,m,lmij->ij", c, c, Bm)
+        Si = np.linalg.inv(S)
+        g1 = np.einsum("m,lmij,ji->l", c, Bm, Si)
+        g2 = np.einsum("m,lmij,ji->l", c, A, Si @ Q @ Si)
+        return float(np.trace(Si @ Q)), 2.0 * (g1 - g2)
+    r = so.minimize(f, c0, jac=True, method="BFGS", options={"maxiter": 200, "gtol": 1e-12})
+    return r.x / np.linalg.norm(r.x), float(r.fun)
+
+
+def measure_fitted_poly(sped, torch, dev, stream, k=3, degree=31, cap=60):
+    """Fitted polynomial coefficients (the paper names meta-learning the coefficients as future
+    work, Section 6): on the 3-room grid world of Section 5.3 (k = 3), every Oja step (eta = 0,
+    FP64) computes the Chebyshev block moments V^T T_l V, l <= 2d + 1, on [0, lambda_bound]
+    (2d + 1 chain steps and 2d + 2 Grams on the device), fits the degree-d coefficients on the
+    host to minimise the sum of the Ritz values of L on span(M V), and applies the fitted M.
+    Steps and SpMMs to a largest principal angle <= 1e-3 against the dense eigendecomposition,
+    beside the fixed operators of the three_room measurement."""
+    g = gen.three_room_grid(2, 10)
+    n = g.n
+    Ld = np.zeros((n, n))
+    rows = np.repeat(np.arange(n), np.diff(g.row_ptr))
+    Ld[rows, g.col_idx] = -1.0
+    Ld[np.arange(n), np.arange(n)] = -Ld.sum(axis=1)
+    lam, U = np.linalg.eigh(Ld)
+    Ud = sped.alloc_block(n, k, torch.float64, dev)
+    Ud[:, :k] = torch.from_numpy(U[:, :k]).to(dev)
+    G = sped.Graph.from_csr(g, device=dev)
+    lb = G.info().lambda_bound
+    d = degree
+    # start: Chebyshev interpolant of exp(-2 lambda) on [0, lb]
+    nodes = np.cos(np.pi * (np.arange(4 * d) + 0.5) / (4 * d))
+    fx = np.exp(-2.0 * (nodes + 1.0) * lb / 2.0)
+    c = np.array([(2.0 - (j == 0)) / (4 * d) * np.sum(fx * np.cos(j * np.arccos(nodes)))
+                  for j in range(d + 1)])
+    V = sped.alloc_block(n, k, torch.float64, dev)
+    V[:, :k] = torch.from_numpy(gen.gaussian_block(n, k, seed=SEED + 29)).to(dev)
+    opts = sped.step_opts(sped.OJA, 0.0, torch.float64, torch.float64)
+    steps, ang, fits = None, None, []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    host_s = 0.0
+    for t in range(1, cap + 1):
+        mu = sped.poly_moments(G, V, k, 2 * d + 2, basis="chebyshev", a=0.0, b=lb)
+        mu = mu.cpu().numpy()
+        h0 = time.perf_counter()
+        c, fval = _fit_chebyshev(mu, d, k, 0.0, lb, c)
+        host_s += time.perf_counter() - h0
+        fits.append(fval)
+        G.set_polynomial(sped.POLY_CHEBYSHEV, d, eps=0.0, coeffs=c, lambda_star=lb)
+        sped.eig_step(G, V, k, opts)
+        ang = _principal_angle(sped, Ud, V, k)
+        if ang <= 1e-3:
+            steps = t
+            break
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    return {"graph": g.name, "n": n, "k": k, "degree": d, "solver": "oja_fp64",
+            "steps": steps, "final_angle": ang,
+            "spmm": None if steps is None else steps * (2 * d + 1 + d),
+            "ritz_sum_fitted_last": fits[-1], "ritz_sum_exact": float(lam[:k].sum()),
+            "wall_s": wall, "host_fit_s": host_s}
+
+
 def measure_batched(sped, torch, dev, stream, k=8, degree=31, steps=4, n_graphs=4096):
     """Many independent graphs in one persistent launch (Section 5 applied per graph): 4,096
     SBMs with log-uniform sizes in [200, 20,000], 2-8 blocks, mean degree 12, 87.5 % of edge
@@ -948,7 +1029,8 @@ def run_ours(args, rank, world, local_rank):
                                                n_graphs=args.batched_graphs),
             "permuted_node_order": lambda: measure_permuted(sped, torch, dev, stream, k, ell),
             "degree_sweep": lambda: measure_degree_sweep(sped, torch, dev, stream),
-            "three_room": lambda: measure_three_room(sped, torch, dev, stream)}
+            "three_room": lambda: measure_three_room(sped, torch, dev, stream),
+            "fitted_poly": lambda: measure_fitted_poly(sped, torch, dev, stream)}
         # gathered bytes of one chain step (every stored entry pulls one k-column row)
         extra["gather_bytes_per_launch"] = g.nnz * k * 2
         for name, fn in runs.items():
@@ -1004,7 +1086,7 @@ def main():
     ap.add_argument("--only-extra", default=None,
                     help="comma list of the extra measurements to run (stochastic, minibatch, "
                          "differentiable, batched, permuted_node_order, degree_sweep, "
-                         "three_room); default all")
+                         "three_room, fitted_poly); default all")
     ap.add_argument("--batched-graphs", type=int, default=4096,
                     help="number of graphs of the batched measurement")
     ap.add_argument("--power-law", action="store_true",

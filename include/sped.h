@@ -137,6 +137,20 @@ sped_status sped_set_polynomial(sped_graph *g, sped_poly_kind kind, int degree, 
 /* Power-basis coefficients c_0..c_l of the operator M = sum_i c_i L^i (h_out: l+1 doubles). */
 sped_status sped_get_power_coeffs(const sped_graph *g, double *h_out, int capacity);
 
+/* Block moments of a polynomial basis on span(V), the data for fitting (meta-learning) the
+ * coefficients of M = sum_l c_l B_l, which the paper names as future work (Section 6):
+ *   d_out[l*k*k + i*k + j] = (V^T B_l V)_{ij},  l = 0 .. n_moments-1 (FP64, device),
+ * basis 0: B_l = L^l; basis 1: B_l = T_l(x), x = (2L - (a + b) I) / (b - a) (b = 0: the
+ * spectral bound). Then V^T M V = sum_l c_l Omega_l; for the power basis (MV)^T (MV) =
+ * sum_{l,m} c_l c_m Omega_{l+m} and (MV)^T L (MV) = sum c_l c_m Omega_{l+m+1}; for the Chebyshev
+ * basis T_l T_m = (T_{l+m} + T_{|l-m|}) / 2 and x T_m = (T_{m+1} + T_{|m-1|}) / 2. One chain step
+ * and one Gram per moment. V: F32 or F64, k <= 32. Scratch: sped_poly_moments_scratch_size. */
+sped_status sped_poly_moments(const sped_graph *g, const void *d_V, sped_dtype v_t, int k, int ld,
+                              int basis, int n_moments, double a, double b, double *d_out,
+                              void *d_scratch, size_t scratch_bytes, void *stream);
+sped_status sped_poly_moments_scratch_size(const sped_graph *g, int k, sped_dtype v_t,
+                                           size_t *bytes);
+
 /* ------------------------------------------------------------------------------------
  * One fused step of the polynomial chain (the hot kernel):
  *   Y[r,:] = alpha V[r,:] + gamma X[r,:] + beta (d_r X[r,:] - sum_j w_rj X[j,:])

@@ -118,6 +118,8 @@ def lib():
         "sped_autotune_scratch_size": [vp, i32, i32, P(sz)],
         "sped_autotune": [vp, i32, i32, vp, sz, vp, P(sped_tune_report)],
         "sped_set_schedule": [vp, i32, i32],
+        "sped_poly_moments": [vp, vp, i32, i32, i32, i32, i32, dbl, dbl, vp, vp, sz, vp],
+        "sped_poly_moments_scratch_size": [vp, i32, i32, P(sz)],
         "sped_sample_edges": [vp, u64, ctypes.c_uint32, i64, i32, vp, vp, vp, vp, vp],
         "sped_edge_step": [i64, i32, vp, vp, vp, i64, dbl, vp, i32, i32, vp, i32, i32, vp, i32,
                            i32, dbl, dbl, dbl, vp, vp],
@@ -321,6 +323,20 @@ def apply_poly(g: Graph, V, Y, k, chain_dtype=None, mode=EXACT, walkers=0, seed=
                                  int(walkers), int(seed), _ptr(scratch), scratch.numel(),
                                  _stream(stream)))
     return Y
+
+
+def poly_moments(g: Graph, V, k, n_moments, basis="chebyshev", a=0.0, b=0.0, stream=None):
+    """Block moments V^T B_l V (FP64, n_moments x k x k) of the power ("power") or Chebyshev
+    ("chebyshev", on [a, b]; b = 0: the spectral bound) basis."""
+    vt, ld = _block(V, k)
+    nb = ctypes.c_size_t()
+    _check(lib().sped_poly_moments_scratch_size(g.handle, k, vt, ctypes.byref(nb)))
+    scr = _scratch(nb.value, V.device)
+    out = torch.empty((n_moments, k, k), dtype=torch.float64, device=V.device)
+    _check(lib().sped_poly_moments(g.handle, _ptr(V), vt, k, ld, 0 if basis == "power" else 1,
+                                   int(n_moments), float(a), float(b), _ptr(out), _ptr(scr),
+                                   nb.value, _stream(stream)))
+    return out
 
 
 def sample_edges(g: Graph, seed, step, count, stratified=False, stream=None):
