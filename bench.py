@@ -222,7 +222,7 @@ TTK_ARMS = {
 }
 
 
-def time_to_bottom_k(sped, torch, g, k, dev, stream, ell_ref, ref_steps=14):
+def time_to_bottom_k(sped, torch, g, k, dev, stream, ell_ref, ref_steps=14, seed=SEED):
     """Time to reach a largest principal angle <= 1e-3 to the bottom-k subspace, per arm.
 
     Reference subspace: FP64 subspace iteration on the dilated operator (l = ell_ref) run far
@@ -233,12 +233,12 @@ def time_to_bottom_k(sped, torch, g, k, dev, stream, ell_ref, ref_steps=14):
     dt = {"bf16": torch.bfloat16, "f32": torch.float32, "f64": torch.float64}
     G = sped.Graph.from_csr(g, device=dev)
     n = g.n
-    V0 = torch.from_numpy(gen.gaussian_block(n, k, seed=SEED)).to(dev)
+    V0 = torch.from_numpy(gen.gaussian_block(n, k, seed=seed)).to(dev)
     G.set_polynomial(sped.POLY_LIMIT_EXP, ell_ref)
     # reference: k + 4 vectors (the extra ones speed it up and estimate lambda_{k+1})
     kp = k + 4
     Vs = sped.alloc_block(n, kp, torch.float64, dev)
-    Vs[:, :kp] = torch.from_numpy(gen.gaussian_block(n, kp, seed=SEED + 31)).to(dev)
+    Vs[:, :kp] = torch.from_numpy(gen.gaussian_block(n, kp, seed=seed + 31)).to(dev)
     Vs[:, :k] = V0
     ref_opts = sped.step_opts(sped.OJA, 0.0, torch.float64, torch.float64)
     stats = torch.zeros(3 * kp, dtype=torch.float64, device=dev)
@@ -1063,6 +1063,17 @@ def run_ours(args, rank, world, local_rank):
         extra["time_to_bottom_k"] = {
             "sbm_n2000_b4_k4": time_to_bottom_k(sped, torch, g1, 4, dev, stream, 45),
             "sbm_regular_n1e6_b20_k20": time_to_bottom_k(sped, torch, g2, k, dev, stream, 41)}
+        # the small workload again with seeds 0, 1, 2 (graph and V0): steps and times per arm
+        per_seed = {}
+        for sd in (0, 1, 2):
+            gs = gen.sbm(2000, 4, 0.05, 0.001, seed=sd)
+            gs.name = f"sbm_n2000_b4_k4_seed{sd}"
+            r = time_to_bottom_k(sped, torch, gs, 4, dev, stream, 45, seed=sd)
+            per_seed[sd] = {a: {"steps": r[a]["steps"], "ms": r[a].get("ms")}
+                            for a in TTK_ARMS}
+            per_seed[sd]["speedup_best_dilated_vs_plain_fp64"] = \
+                r.get("speedup_best_dilated_vs_plain_fp64")
+        extra["time_to_bottom_k"]["sbm_n2000_b4_k4_seeds_0_1_2"] = per_seed
     clocks = clk.summary()
     if rank != 0:
         return
