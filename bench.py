@@ -776,9 +776,28 @@ def measure_batched(sped, torch, dev, stream, k=8, degree=31, steps=4, n_graphs=
     V[:, :k] = torch.from_numpy(gen.gaussian_block(n, k, seed=SEED + 13)).to(dev)
     scr = torch.empty(B.scratch_bytes(k), dtype=torch.uint8, device=dev)
     ritz = torch.empty((B.n_graphs, k), dtype=torch.float64, device=dev)
+    B.set_schedule(512, 2)
     run = lambda: B.eig_steps(V, k, steps=steps, eta=1.0, ritz=ritz, scratch=scr)
     run()
+    ms_default = _timed(torch, stream, run, 3) / steps
+    tune = B.autotune(V, k)  # picks threads per CTA and CTAs per SM for this batch
+    run()
     ms = _timed(torch, stream, run, 3) / steps
+    # the same call captured once in a CUDA graph and replayed
+    graph_ms = None
+    try:
+        side = torch.cuda.Stream()
+        side.wait_stream(stream)
+        cg = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(cg, stream=side):
+                B.eig_steps(V, k, steps=steps, eta=1.0, ritz=ritz, scratch=scr, stream=side)
+        stream.wait_stream(side)
+        cg.replay()
+        torch.cuda.synchronize()
+        graph_ms = _timed(torch, stream, cg.replay, 3) / steps
+    except Exception as exc:  # capture is optional: report why it was skipped
+        graph_ms = f"skipped: {type(exc).__name__}: {exc}"
     step_b = degree * spmm_bytes(n, nnz, k, 2, 2) + n * k * 4 * 2 + n * k * 4 * 3
     peak, kind = _peaks()
     return {"workload": f"batched_sbm_{B.n_graphs}graphs_n{n}_k{k}", "graphs": B.n_graphs,
@@ -786,7 +805,10 @@ def measure_batched(sped, torch, dev, stream, k=8, degree=31, steps=4, n_graphs=
             "ms_per_step": ms, "graph_steps_per_s": B.n_graphs / (ms * 1e-3),
             "step_bytes": step_b, "gbs": step_b / (ms * 1e-3) / 1e9,
             "frac_of_hbm": step_b / (ms * 1e-3) / 1e9 / peak, "peak_kind": kind,
-            "launches_per_call": 1, "steps_per_call": steps}
+            "launches_per_call": 1, "steps_per_call": steps,
+            "schedule": {"threads": tune["threads"], "ctas_per_sm": tune["ctas_per_sm"],
+                         "candidate_ms": tune["ms"], "default_512x2_ms_per_step": ms_default},
+            "cuda_graph_replay_ms_per_step": graph_ms}
 
 
 def measure_differentiable(sped, torch, dev, stream, k=10, ell=11, reps=5):

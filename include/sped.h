@@ -437,6 +437,29 @@ sped_status sped_batch_eig_steps(const sped_batch *b, int steps, double eta, spe
                                  float *d_V, int k, int ld, double *d_ritz, void *d_scratch,
                                  size_t scratch_bytes, void *stream);
 
+/* Schedule of the batched launch: threads per CTA (128, 256 or 512; a thread per row, so small
+ * graphs idle fewer lanes in smaller CTAs) and CTAs per SM (how many graphs are in flight).
+ * Default 512 threads, 2 CTAs per SM. sped_batch_autotune times one solver step (eta = 1) per
+ * candidate {512,2} {512,4} {256,4} {256,8} {128,8} {128,16} on a copy of d_V (V itself is not
+ * changed), keeps the fastest in the batch handle and in a per-process table keyed by the
+ * batch's shape (graphs, nodes, entries, degree, weighted, k, chain dtype, device); a later
+ * batch of the same shape takes it from there (report->cached = 1). Synchronises `stream`.
+ * Scratch: sped_batch_autotune_scratch_size bytes (256-byte aligned). */
+typedef struct {
+    int threads;       /* chosen threads per CTA                                 */
+    int ctas_per_sm;   /* chosen CTAs per SM                                     */
+    int cached;        /* 1: taken from the per-process table, nothing was timed */
+    int n_candidates;  /* entries of ms[] filled                                 */
+    double ms[8];      /* one solver step per candidate, in the order above      */
+} sped_batch_tune_report;
+
+sped_status sped_batch_set_schedule(sped_batch *b, int threads, int ctas_per_sm);
+sped_status sped_batch_autotune_scratch_size(const sped_batch *b, int k, sped_dtype chain_t,
+                                             size_t *bytes);
+sped_status sped_batch_autotune(sped_batch *b, int k, sped_dtype chain_t, const float *d_V,
+                                int ld, void *d_scratch, size_t scratch_bytes, void *stream,
+                                sped_batch_tune_report *report);
+
 /* ------------------------------------------------------------------------------------
  * Differentiable utilities (the solver family of Section 5.1 as a loss): with H = V^T M V
  * (k x k, e.g. the block H = G[0:k, k:2k] of sped_gram(V, M V), ldh = 2k),

@@ -68,6 +68,11 @@ class sped_tune_report(ctypes.Structure):
                 ("n_candidates", ctypes.c_int), ("ms", ctypes.c_double * 8)]
 
 
+class sped_batch_tune_report(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("cached", ctypes.c_int),
+                ("n_candidates", ctypes.c_int), ("ms", ctypes.c_double * 8)]
+
+
 class sped_solve_report(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int), ("phase1_steps", ctypes.c_int),
                 ("spmm_count", ctypes.c_int64), ("final_residual", ctypes.c_double),
@@ -562,6 +567,22 @@ class Batch:
                                              ctypes.byref(nb)))
         return nb.value
 
+    def set_schedule(self, threads=512, ctas_per_sm=2):
+        _check(lib().sped_batch_set_schedule(self.handle, int(threads), int(ctas_per_sm)))
+
+    def autotune(self, V, k, chain_dtype=torch.bfloat16, stream=None):
+        """Time the candidate schedules on a copy of V; the fastest is kept (dict report)."""
+        nb = ctypes.c_size_t()
+        _check(lib().sped_batch_autotune_scratch_size(self.handle, k, _TORCH_DT[chain_dtype],
+                                                      ctypes.byref(nb)))
+        scr = _scratch(nb.value, V.device)
+        rep = sped_batch_tune_report()
+        _check(lib().sped_batch_autotune(self.handle, k, _TORCH_DT[chain_dtype], _ptr(V),
+                                         V.stride(0), _ptr(scr), nb.value, _stream(stream),
+                                         ctypes.byref(rep)))
+        return dict(threads=rep.threads, ctas_per_sm=rep.ctas_per_sm, cached=bool(rep.cached),
+                    ms=[rep.ms[i] for i in range(rep.n_candidates)])
+
     def eig_steps(self, V, k, steps=1, eta=1.0, chain_dtype=torch.bfloat16, ritz=None,
                   scratch=None, stream=None):
         if V.dtype != torch.float32 or V.dim() != 2 or V.stride(1) != 1:
@@ -598,6 +619,9 @@ def _batch_sigs(L):
         "sped_batch_scale": [vp, P(dbl), i32],
         "sped_batch_scratch_size": [vp, i32, i32, P(sz)],
         "sped_batch_eig_steps": [vp, i32, dbl, i32, vp, i32, i32, vp, vp, sz, vp],
+        "sped_batch_set_schedule": [vp, i32, i32],
+        "sped_batch_autotune_scratch_size": [vp, i32, i32, P(sz)],
+        "sped_batch_autotune": [vp, i32, i32, vp, i32, vp, sz, vp, P(sped_batch_tune_report)],
     }.items():
         f = getattr(L, name)
         f.argtypes = args

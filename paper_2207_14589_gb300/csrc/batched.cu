@@ -4,6 +4,15 @@
 // of the limit form (I - s_g L_g)^l (Table 2), the Gram [V Y]^T [V Y], the FP64 k x k mu-EG
 // algebra (Section 5.1) and the N_g x k update. No CTA ever waits for another, so the launch
 // is safe to capture in a CUDA graph and replay.
+//
+// Schedule: threads per CTA (128, 256 or 512: a thread per row in the chain steps and the
+// update, so small graphs waste fewer idle lanes with smaller CTAs) and CTAs per SM (the grid,
+// and with it how many graphs are in flight). sped_batch_autotune times one solver step per
+// candidate on the caller's batch and keeps the fastest in the handle; a per-process table
+// keyed by the batch's shape serves later batches of the same shape.
+#include <cstring>
+#include <mutex>
+#include <unordered_map>
 #include <algorithm>
 #include <cmath>
 #include <numeric>
@@ -23,11 +32,12 @@ struct sped_batch {
     int32_t *d_counter;  // work-list counter
     std::vector<int64_t> h_off;
     std::vector<double> h_bound, h_scale;
+    int threads = 512;     // schedule: threads per CTA
+    int ctas_per_sm = 2;   // and CTAs per SM
 };
 
 namespace sped {
 
-constexpr int BT = 512;
 constexpr int BMAXK = 16;
 
 struct BatchArgs {
@@ -52,7 +62,7 @@ struct BatchArgs {
 };
 
 // One chain step over rows [r0, r1): out = (1 - s d) x + s sum_j w_j x_j, thread per row.
-template <typename Ti, typename To, bool W, int KP>
+template <typename Ti, typename To, bool W, int KP, int BT>
 __device__ __forceinline__ void batch_chain_step(const BatchArgs &a, int r0, int r1, float s,
                                                  const Ti *X, int ldx, To *Yo, int ldo) {
     constexpr int E = 16 / (int)sizeof(Ti);
@@ -88,7 +98,7 @@ __device__ __forceinline__ void batch_chain_step(const BatchArgs &a, int r0, int
     }
 }
 
-template <typename Tc, bool W, int KP>
+template <typename Tc, bool W, int KP, int BT>
 __global__ void __launch_bounds__(BT) k_batch(BatchArgs a) {
     constexpr int K2 = 2 * KP;
     constexpr int NB = K2 / 4;
@@ -129,13 +139,17 @@ __global__ void __launch_bounds__(BT) k_batch(BatchArgs a) {
                 Tc *xin = (Tc *)((c - 1) % 2 == 0 ? a.Xb0 : a.Xb1);
                 Tc *xout = (Tc *)(c % 2 == 0 ? a.Xb0 : a.Xb1);
                 if (first && last)
-                    batch_chain_step<float, float, W, KP>(a, r0, r1, s, a.V, a.ldv, a.Y, a.ldy);
+                    batch_chain_step<float, float, W, KP, BT>(a, r0, r1, s, a.V, a.ldv, a.Y,
+                                                              a.ldy);
                 else if (first)
-                    batch_chain_step<float, Tc, W, KP>(a, r0, r1, s, a.V, a.ldv, xout, a.ldc);
+                    batch_chain_step<float, Tc, W, KP, BT>(a, r0, r1, s, a.V, a.ldv, xout,
+                                                           a.ldc);
                 else if (last)
-                    batch_chain_step<Tc, float, W, KP>(a, r0, r1, s, xin, a.ldc, a.Y, a.ldy);
+                    batch_chain_step<Tc, float, W, KP, BT>(a, r0, r1, s, xin, a.ldc, a.Y,
+                                                           a.ldy);
                 else
-                    batch_chain_step<Tc, Tc, W, KP>(a, r0, r1, s, xin, a.ldc, xout, a.ldc);
+                    batch_chain_step<Tc, Tc, W, KP, BT>(a, r0, r1, s, xin, a.ldc, xout,
+                                                        a.ldc);
                 __syncthreads();
             }
             // ---- Gram of [V Y] over the graph's rows (F32 per worker, F64 in shared memory)
@@ -290,6 +304,112 @@ static size_t batch_scratch_bytes(const sped_batch *b, int k, sped_dtype ct) {
     return p.total();
 }
 
+// the solver steps with an explicit schedule (threads per CTA, CTAs per SM)
+static sped_status batch_steps(const sped_batch *b, int steps, double eta, sped_dtype chain_t,
+                               float *d_V, int k, int ld, double *d_ritz, void *d_scratch,
+                               size_t scratch_bytes, cudaStream_t st, int threads, int cps) {
+    if (steps < 1 || !(eta > 0.0) || !std::isfinite(eta))
+        return fail(SPED_ERR_INVALID_ARG, "batch_eig_steps: steps >= 1 and eta > 0 required");
+    if (k < 1 || k > BMAXK) return fail(SPED_ERR_UNSUPPORTED, "batch_eig_steps: k <= %d", BMAXK);
+    if (chain_t != SPED_BF16 && chain_t != SPED_F32)
+        return fail(SPED_ERR_INVALID_ARG, "batch_eig_steps: chain must be BF16 or F32");
+    const int KP = k <= 8 ? 8 : 16;
+    if (ld < KP || ((uintptr_t)d_V) % 16)
+        return fail(SPED_ERR_INVALID_ARG, "batch_eig_steps: V needs ld >= %d and 16-byte "
+                                          "alignment", KP);
+    const size_t need = batch_scratch_bytes(b, k, chain_t);
+    if (!d_scratch || scratch_bytes < need || ((uintptr_t)d_scratch) % 256)
+        return fail(SPED_ERR_SCRATCH, "batch_eig_steps: scratch needs %zu bytes", need);
+    Scratch scr(d_scratch, scratch_bytes);
+    BatchArgs a;
+    a.rp = b->rp;
+    a.ci = b->ci;
+    a.w = b->w;
+    a.order = b->d_order;
+    a.off = b->d_off;
+    a.scale = b->d_scale;
+    a.counter = b->d_counter;
+    a.n_graphs = (int)b->n_graphs;
+    a.ell = b->ell;
+    a.steps = steps;
+    a.k = k;
+    a.eta = eta;
+    a.V = d_V;
+    a.ldv = ld;
+    a.Y = (float *)scr.take((size_t)b->n_total * KP * 4);
+    a.ldy = KP;
+    a.Xb0 = scr.take((size_t)b->n_total * KP * dtype_size(chain_t));
+    a.Xb1 = scr.take((size_t)b->n_total * KP * dtype_size(chain_t));
+    a.ldc = KP;
+    a.status = (int *)scr.take(sizeof(int) * 4);
+    a.ritz = d_ritz;
+    SPED_CUDA(cudaMemsetAsync(b->d_counter, 0, sizeof(int32_t), st));
+    SPED_CUDA(cudaMemsetAsync(a.status, 0, sizeof(int), st));
+    const int grid = device_sm_count() * cps;
+    const bool W = b->w != nullptr;
+#define LAUNCH(TC, WW, KK, NT) k_batch<TC, WW, KK, NT><<<grid, NT, 0, st>>>(a)
+#define LAUNCH_T(TC, WW, KK)                            \
+    do {                                                \
+        if (threads == 128) LAUNCH(TC, WW, KK, 128);    \
+        else if (threads == 256) LAUNCH(TC, WW, KK, 256); \
+        else LAUNCH(TC, WW, KK, 512);                   \
+    } while (0)
+    if (chain_t == SPED_BF16) {
+        if (KP == 8) { if (W) LAUNCH_T(__nv_bfloat16, true, 8); else LAUNCH_T(__nv_bfloat16, false, 8); }
+        else { if (W) LAUNCH_T(__nv_bfloat16, true, 16); else LAUNCH_T(__nv_bfloat16, false, 16); }
+    } else {
+        if (KP == 8) { if (W) LAUNCH_T(float, true, 8); else LAUNCH_T(float, false, 8); }
+        else { if (W) LAUNCH_T(float, true, 16); else LAUNCH_T(float, false, 16); }
+    }
+#undef LAUNCH_T
+#undef LAUNCH
+    SPED_CHECK_LAUNCH("k_batch");
+    return SPED_OK;
+}
+
+// schedule candidates: {threads per CTA, CTAs per SM}
+constexpr int BTUNE[][2] = {{512, 2}, {512, 4}, {256, 4}, {256, 8}, {128, 8}, {128, 16}};
+constexpr int BTUNE_N = (int)(sizeof(BTUNE) / sizeof(BTUNE[0]));
+
+static std::mutex g_btune_mu;
+static std::unordered_map<uint64_t, std::pair<int, int>> g_btune;
+
+static uint64_t batch_shape_key(const sped_batch *b, int k, sped_dtype ct) {
+    uint64_t h = 0x42415443ull;
+    auto mix = [&](uint64_t v) { h ^= v + 0x9E3779B97F4A7C15ull + (h << 6) + (h >> 2); };
+    mix((uint64_t)b->n_graphs);
+    mix((uint64_t)b->n_total);
+    mix((uint64_t)b->nnz);
+    mix((uint64_t)b->ell);
+    mix(b->w != nullptr);
+    mix((uint64_t)k);
+    mix((uint64_t)ct);
+    mix((uint64_t)b->device);
+    mix((uint64_t)device_sm_count());
+    return h;
+}
+
+struct BatchTuneLayout {
+    size_t v, ritz, steps, total;
+};
+
+static BatchTuneLayout batch_tune_layout(const sped_batch *b, int k, sped_dtype ct) {
+    BatchTuneLayout L;
+    const int KP = k <= 8 ? 8 : 16;
+    ScratchPlan p;
+    L.v = 0;
+    p.add((size_t)b->n_total * 16 * sizeof(float));  // copy of V (ld up to 16)
+    p.used = align_up(p.used, 256);
+    L.ritz = p.used;
+    p.add(sizeof(double) * (size_t)b->n_graphs * BMAXK);
+    p.used = align_up(p.used, 256);
+    L.steps = p.used;
+    p.add(batch_scratch_bytes(b, k, ct));
+    L.total = p.total();
+    (void)KP;
+    return L;
+}
+
 }  // namespace sped
 
 using namespace sped;
@@ -412,57 +532,114 @@ sped_status sped_batch_eig_steps(const sped_batch *b, int steps, double eta, spe
                                  float *d_V, int k, int ld, double *d_ritz, void *d_scratch,
                                  size_t scratch_bytes, void *stream) {
     if (!b || !d_V || !d_ritz) return fail(SPED_ERR_INVALID_ARG, "batch_eig_steps: null");
-    if (steps < 1 || !(eta > 0.0) || !std::isfinite(eta))
-        return fail(SPED_ERR_INVALID_ARG, "batch_eig_steps: steps >= 1 and eta > 0 required");
-    if (k < 1 || k > BMAXK) return fail(SPED_ERR_UNSUPPORTED, "batch_eig_steps: k <= %d", BMAXK);
-    if (chain_t != SPED_BF16 && chain_t != SPED_F32)
-        return fail(SPED_ERR_INVALID_ARG, "batch_eig_steps: chain must be BF16 or F32");
+    return batch_steps(b, steps, eta, chain_t, d_V, k, ld, d_ritz, d_scratch, scratch_bytes,
+                       as_stream(stream), b->threads, b->ctas_per_sm);
+}
+
+sped_status sped_batch_set_schedule(sped_batch *b, int threads, int ctas_per_sm) {
+    if (!b) return fail(SPED_ERR_INVALID_ARG, "batch_set_schedule: null batch");
+    if (threads != 128 && threads != 256 && threads != 512)
+        return fail(SPED_ERR_INVALID_ARG, "batch_set_schedule: threads %d not 128, 256 or 512",
+                    threads);
+    if (ctas_per_sm < 1 || ctas_per_sm > 16)
+        return fail(SPED_ERR_INVALID_ARG, "batch_set_schedule: %d CTAs per SM not in 1..16",
+                    ctas_per_sm);
+    b->threads = threads;
+    b->ctas_per_sm = ctas_per_sm;
+    return SPED_OK;
+}
+
+sped_status sped_batch_autotune_scratch_size(const sped_batch *b, int k, sped_dtype chain_t,
+                                             size_t *bytes) {
+    if (!b || !bytes || k < 1 || k > BMAXK || (chain_t != SPED_BF16 && chain_t != SPED_F32))
+        return fail(SPED_ERR_INVALID_ARG, "batch_autotune_scratch_size: bad arguments");
+    *bytes = batch_tune_layout(b, k, chain_t).total;
+    return SPED_OK;
+}
+
+sped_status sped_batch_autotune(sped_batch *b, int k, sped_dtype chain_t, const float *d_V,
+                                int ld, void *d_scratch, size_t scratch_bytes, void *stream,
+                                sped_batch_tune_report *rep) {
+    if (!b || !d_V || k < 1 || k > BMAXK || (chain_t != SPED_BF16 && chain_t != SPED_F32))
+        return fail(SPED_ERR_INVALID_ARG, "batch_autotune: bad arguments");
     const int KP = k <= 8 ? 8 : 16;
     if (ld < KP || ((uintptr_t)d_V) % 16)
-        return fail(SPED_ERR_INVALID_ARG, "batch_eig_steps: V needs ld >= %d and 16-byte "
-                                          "alignment", KP);
-    const size_t need = batch_scratch_bytes(b, k, chain_t);
-    if (!d_scratch || scratch_bytes < need || ((uintptr_t)d_scratch) % 256)
-        return fail(SPED_ERR_SCRATCH, "batch_eig_steps: scratch needs %zu bytes", need);
-    cudaStream_t st = as_stream(stream);
-    Scratch scr(d_scratch, scratch_bytes);
-    BatchArgs a;
-    a.rp = b->rp;
-    a.ci = b->ci;
-    a.w = b->w;
-    a.order = b->d_order;
-    a.off = b->d_off;
-    a.scale = b->d_scale;
-    a.counter = b->d_counter;
-    a.n_graphs = (int)b->n_graphs;
-    a.ell = b->ell;
-    a.steps = steps;
-    a.k = k;
-    a.eta = eta;
-    a.V = d_V;
-    a.ldv = ld;
-    a.Y = (float *)scr.take((size_t)b->n_total * KP * 4);
-    a.ldy = KP;
-    a.Xb0 = scr.take((size_t)b->n_total * KP * dtype_size(chain_t));
-    a.Xb1 = scr.take((size_t)b->n_total * KP * dtype_size(chain_t));
-    a.ldc = KP;
-    a.status = (int *)scr.take(sizeof(int) * 4);
-    a.ritz = d_ritz;
-    SPED_CUDA(cudaMemsetAsync(b->d_counter, 0, sizeof(int32_t), st));
-    SPED_CUDA(cudaMemsetAsync(a.status, 0, sizeof(int), st));
-    const int grid = device_sm_count() * 2;
-#define LAUNCH(TC, WW, KK) k_batch<TC, WW, KK><<<grid, BT, 0, st>>>(a)
-    const bool W = b->w != nullptr;
-    if (chain_t == SPED_BF16) {
-        if (KP == 8) { if (W) LAUNCH(__nv_bfloat16, true, 8); else LAUNCH(__nv_bfloat16, false, 8); }
-        else { if (W) LAUNCH(__nv_bfloat16, true, 16); else LAUNCH(__nv_bfloat16, false, 16); }
-    } else {
-        if (KP == 8) { if (W) LAUNCH(float, true, 8); else LAUNCH(float, false, 8); }
-        else { if (W) LAUNCH(float, true, 16); else LAUNCH(float, false, 16); }
+        return fail(SPED_ERR_INVALID_ARG, "batch_autotune: V needs ld >= %d, 16-byte aligned", KP);
+    sped_batch_tune_report r;
+    std::memset(&r, 0, sizeof(r));
+    const uint64_t key = batch_shape_key(b, k, chain_t);
+    {
+        std::lock_guard<std::mutex> lk(g_btune_mu);
+        auto it = g_btune.find(key);
+        if (it != g_btune.end()) {
+            b->threads = it->second.first;
+            b->ctas_per_sm = it->second.second;
+            r.threads = b->threads;
+            r.ctas_per_sm = b->ctas_per_sm;
+            r.cached = 1;
+            if (rep) *rep = r;
+            return SPED_OK;
+        }
     }
-#undef LAUNCH
-    SPED_CHECK_LAUNCH("k_batch");
-    return SPED_OK;
+    const BatchTuneLayout L = batch_tune_layout(b, k, chain_t);
+    if (!d_scratch || scratch_bytes < L.total || ((uintptr_t)d_scratch) % 256)
+        return fail(SPED_ERR_SCRATCH, "batch_autotune: scratch needs %zu bytes (256-aligned)",
+                    L.total);
+    cudaStream_t st = as_stream(stream);
+    char *base = (char *)d_scratch;
+    float *Vc = (float *)(base + L.v);
+    double *ritz = (double *)(base + L.ritz);
+    void *steps_scr = base + L.steps;
+    const size_t steps_bytes = L.total - L.steps;
+    // the copy of V is compact (ld = KP): only the KP columns the kernel reads
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto cleanup = [&](sped_status s) {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        return s;
+    };
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return cleanup(fail(SPED_ERR_CUDA, "batch_autotune: event creation failed"));
+    int best = 0;
+    double best_ms = 1e300;
+    for (int c = 0; c < BTUNE_N; ++c) {
+        const int th = BTUNE[c][0], cps = BTUNE[c][1];
+        // every candidate starts from the caller's V, so all time the same work
+        auto copy_v = [&]() {
+            return cudaMemcpy2DAsync(Vc, sizeof(float) * KP, d_V, sizeof(float) * ld,
+                                     sizeof(float) * KP, (size_t)b->n_total,
+                                     cudaMemcpyDeviceToDevice, st);
+        };
+        if (copy_v() != cudaSuccess)
+            return cleanup(fail(SPED_ERR_CUDA, "batch_autotune: copy of V failed"));
+        sped_status s = batch_steps(b, 1, 1.0, chain_t, Vc, k, KP, ritz, steps_scr, steps_bytes,
+                                    st, th, cps);  // warm-up
+        if (s != SPED_OK) return cleanup(s);
+        if (copy_v() != cudaSuccess || cudaEventRecord(e0, st) != cudaSuccess)
+            return cleanup(fail(SPED_ERR_CUDA, "batch_autotune: timing set-up failed"));
+        s = batch_steps(b, 1, 1.0, chain_t, Vc, k, KP, ritz, steps_scr, steps_bytes, st, th, cps);
+        if (s != SPED_OK) return cleanup(s);
+        float ms = 0.f;
+        if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+            return cleanup(fail(SPED_ERR_CUDA, "batch_autotune: timing failed"));
+        r.ms[c] = ms;
+        r.n_candidates = c + 1;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    b->threads = BTUNE[best][0];
+    b->ctas_per_sm = BTUNE[best][1];
+    {
+        std::lock_guard<std::mutex> lk(g_btune_mu);
+        g_btune[key] = {b->threads, b->ctas_per_sm};
+    }
+    r.threads = b->threads;
+    r.ctas_per_sm = b->ctas_per_sm;
+    if (rep) *rep = r;
+    return cleanup(SPED_OK);
 }
 
 }  // extern "C"

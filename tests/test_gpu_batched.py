@@ -136,3 +136,51 @@ def test_batched_rejects_columns_outside_their_graph():
     with pytest.raises(sped.SpedError) as e:
         sped.Batch(node_off, torch.from_numpy(big.row_ptr).cuda(), torch.from_numpy(ci).cuda())
     assert e.value.status == sped.ERR_BAD_CSR
+
+
+SCHEDULES = [(512, 2), (512, 4), (256, 4), (256, 8), (128, 8), (128, 16)]
+
+
+@pytest.mark.parametrize("threads,cps", SCHEDULES)
+@pytest.mark.parametrize("k", [6, 12])
+def test_batched_every_schedule_matches_oracle(threads, cps, k):
+    graphs = _graphs(20, 200 + k)
+    ell, eta = 7, 0.8
+    B = sped.Batch.from_graphs(graphs, degree=ell)
+    B.set_schedule(threads, cps)
+    scales = B.scales()
+    V = sped.batch_block(B.n_total, k)
+    V[:, :k] = torch.from_numpy(gen.gaussian_block(B.n_total, k, seed=9)).float().cuda()
+    Vs = _split(V[:, :k].double().cpu().numpy(), graphs, k)
+    B.eig_steps(V, k, steps=1, eta=eta, chain_dtype=torch.float32)
+    torch.cuda.synchronize()
+    got = _split(V.double().cpu().numpy(), graphs, k)
+    for i, (g, Vi) in enumerate(zip(graphs, Vs)):
+        want = oracle.mu_eg_step(Vi, oracle.poly_limit(g, Vi, scales[i], ell), eta)
+        assert np.linalg.norm(got[i] - want) / np.linalg.norm(want) <= 1e-4, i
+
+
+def test_batched_autotune_keeps_v_and_a_valid_schedule():
+    graphs = _graphs(40, 77)
+    k = 8
+    B = sped.Batch.from_graphs(graphs, degree=9)
+    V = sped.batch_block(B.n_total, k)
+    V[:, :k] = torch.from_numpy(gen.gaussian_block(B.n_total, k, seed=10)).float().cuda()
+    before = V.clone()
+    rep = B.autotune(V, k)
+    torch.cuda.synchronize()
+    assert torch.equal(V, before)  # timed on a copy
+    assert (rep["threads"], rep["ctas_per_sm"]) in SCHEDULES
+    if not rep["cached"]:
+        assert len(rep["ms"]) == len(SCHEDULES) and all(t > 0 for t in rep["ms"])
+        assert SCHEDULES[int(np.argmin(rep["ms"]))] == (rep["threads"], rep["ctas_per_sm"])
+    again = sped.Batch.from_graphs(graphs, degree=9).autotune(V, k)
+    assert again["cached"] and (again["threads"], again["ctas_per_sm"]) == \
+        (rep["threads"], rep["ctas_per_sm"])
+
+
+def test_batched_set_schedule_rejects_bad_arguments():
+    B = sped.Batch.from_graphs(_graphs(2, 3), degree=3)
+    for th, cps in [(64, 2), (1024, 1), (512, 0), (256, 17)]:
+        with pytest.raises(sped.SpedError):
+            B.set_schedule(th, cps)
