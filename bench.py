@@ -971,6 +971,23 @@ def run_ours(args, rank, world, local_rank):
                 "per_launch_bytes": per_launch_bytes, "launch_us": launch_ms * 1e3,
                 "peak_kind": f"{peak_kind} (copy, burst)"}
 
+    # the chain step against the rate at which this GPU serves the same random row gathers:
+    # the probe replays its access stream without arithmetic (CSR order, hashed rows,
+    # consecutive rows)
+    Xg = sped.alloc_block(g.n, k, torch.bfloat16, dev)
+    Xg[:, :k] = V[:, :k].to(torch.bfloat16)
+    Yg = sped.alloc_block(g.n, k, torch.bfloat16, dev)
+    gather = {"chain_step_us": launch_ms * 1e3, "gathers_per_launch": g.nnz,
+              "bytes_per_gather": sped.padded_ld(k, torch.bfloat16) * 2}
+    for mode, name in ((0, "csr_order"), (1, "hashed_rows"), (2, "consecutive_rows")):
+        probe = lambda: sped.probe_gather(G, Xg, Yg, k, mode=mode, seed=SEED)
+        probe()
+        us = _timed(torch, stream, probe, 20) * 1e3
+        gather[f"{name}_us"] = us
+        gather[f"{name}_gathers_per_s"] = g.nnz / (us * 1e-6)
+    gather["chain_over_csr_order_gathers"] = gather["chain_step_us"] / gather["csr_order_us"]
+    del Xg, Yg
+
     # end to end through the C ABI with host buffers: every step copies its V from pinned host
     # memory, runs, and copies its result back. Two device buffers and two copy streams let
     # the copies of neighbouring steps overlap the current step's kernels (each step's input
@@ -1106,6 +1123,7 @@ def run_ours(args, rank, world, local_rank):
             "gpu_launches": K * (ell + 4),
             "poly_gbs": chain_b / (mean_chain_ms * 1e-3) / 1e9,
             "cuda_graph_replay": graph_rec,
+            "gather_ceiling": gather,
             "step_bytes": step_b}
     line.update(extra)
     if not args.no_cpu:
