@@ -230,6 +230,15 @@ sped_status sped_apply_poly(const sped_graph *g, int k, const void *d_V, sped_dt
 sped_status sped_apply_poly_scratch_size(const sped_graph *g, int k, sped_dtype chain_t,
                                          sped_mode mode, size_t *bytes);
 
+/* Backward of Y = M V with respect to V: dV = M^T dY = M dY, since M = p(L) is symmetric (L is,
+ * Section 2), i.e. the exact chain of sped_apply_poly run on dY (same dtype rules; scratch:
+ * sped_apply_poly_scratch_size with SPED_EXACT). The gradient with respect to the edge weights
+ * of a utility of (V, M V) is sped_edge_grad. */
+sped_status sped_apply_poly_backward(const sped_graph *g, int k, const void *d_dY, sped_dtype dy_t,
+                                     int lddy, void *d_dV, sped_dtype dv_t, int lddv,
+                                     sped_dtype chain_t, void *d_scratch, size_t scratch_bytes,
+                                     void *stream);
+
 /* ------------------------------------------------------------------------------------
  * Edge minibatches fed from outside (Sections 2 and 6: edges arrive in minibatches, or are
  * drawn from a distribution such as a link-prediction model's output).

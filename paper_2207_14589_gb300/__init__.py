@@ -107,6 +107,7 @@ def lib():
         "sped_poly_step_scratch_size": [vp, i32, i32, i32, P(sz)],
         "sped_apply_poly": [vp, i32, vp, i32, i32, vp, i32, i32, i32, i32, i64, u64, vp, sz, vp],
         "sped_apply_poly_scratch_size": [vp, i32, i32, i32, P(sz)],
+        "sped_apply_poly_backward": [vp, i32, vp, i32, i32, vp, i32, i32, i32, vp, sz, vp],
         "sped_gram": [i64, vp, i32, i32, i32, vp, i32, i32, i32, vp, vp, sz, vp],
         "sped_gram_scratch_size": [i64, i32, i32, P(sz)],
         "sped_eig_step": [vp, P(sped_step_opts), vp, i32, i32, i32, vp, vp, sz, vp],
@@ -391,6 +392,18 @@ def edge_step(n, X, Y, k, a, b, w=None, edge_scale=1.0, alpha=0.0, beta=1.0, gam
                                 ldy, float(alpha), float(beta), float(gamma), _ptr(skipped),
                                 _stream(stream)))
     return Y
+
+
+def apply_poly_backward(g: Graph, dY, dV, k, chain_dtype=None, scratch=None, stream=None):
+    """dV = M^T dY = M dY (M = p(L) symmetric): the backward of Y = M V with respect to V."""
+    yt, ldy = _block(dY, k)
+    vt, ldv = _block(dV, k)
+    ct = _TORCH_DT[chain_dtype] if chain_dtype is not None else yt
+    if scratch is None:
+        scratch = _scratch(apply_poly_scratch_bytes(g, k, _DT_TORCH[ct]), dY.device)
+    _check(lib().sped_apply_poly_backward(g.handle, k, _ptr(dY), yt, ldy, _ptr(dV), vt, ldv, ct,
+                                          _ptr(scratch), scratch.numel(), _stream(stream)))
+    return dV
 
 
 def gram(A, ka, B=None, kb=0, G=None, scratch=None, stream=None):

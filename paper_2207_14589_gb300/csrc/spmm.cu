@@ -686,4 +686,19 @@ sped_status sped_apply_poly(const sped_graph *g, int k, const void *d_V, sped_dt
                            as_stream(stream), nullptr, SPED_BF16, 0);
 }
 
+sped_status sped_apply_poly_backward(const sped_graph *g, int k, const void *d_dY, sped_dtype dy_t,
+                                     int lddy, void *d_dV, sped_dtype dv_t, int lddv,
+                                     sped_dtype chain_t, void *d_scratch, size_t scratch_bytes,
+                                     void *stream) {
+    if (!g) return fail(SPED_ERR_INVALID_ARG, "apply_poly_backward: null graph");
+    SPED_TRY(check_layout(d_dY, dy_t, k, lddy, "apply_poly_backward dY"));
+    SPED_TRY(check_layout(d_dV, dv_t, k, lddv, "apply_poly_backward dV"));
+    if (!dtype_valid(chain_t)) return fail(SPED_ERR_INVALID_ARG, "apply_poly_backward: chain dtype");
+    if (d_dY == d_dV) return fail(SPED_ERR_INVALID_ARG, "apply_poly_backward: dY and dV alias");
+    // M = p(L) is symmetric (L is), so the adjoint of V -> M V is M itself: the same chain
+    Scratch scr(d_scratch, scratch_bytes);
+    return apply_poly_impl(g, k, d_dY, dy_t, lddy, d_dV, dv_t, lddv, chain_t, SPED_EXACT, 0, 0, scr,
+                           as_stream(stream), nullptr, SPED_BF16, 0);
+}
+
 }  // extern "C"

@@ -9,7 +9,7 @@ import torch
 import gen
 import oracle
 import paper_2207_14589_gb300 as sped
-from util_gpu import DEV, rel, to_block
+from util_gpu import DEV, host, rel, to_block
 
 pytestmark = pytest.mark.gpu
 
@@ -104,3 +104,29 @@ def test_edge_grad_full_size_spot_check():
     got = sped.edge_grad(G, V, k, torch.tensor(Hb.T.copy(), device=DEV)).cpu().numpy()
     want = oracle.limit_edge_grad(g, V0, info.scale_s, ell, Hb)
     assert rel(got, want) <= 1e-9
+
+
+@pytest.mark.parametrize("kind", ["limit", "chebyshev"])
+def test_apply_poly_backward_is_the_adjoint(kind):
+    # <dY, M V> = <M^T dY, V> with M = p(L) symmetric, and dV matches the oracle's M dY
+    g = gen.uniform_edge_weights(gen.random_graph(800, 3000, seed=71), seed=72)
+    G = sped.Graph.from_csr(g)
+    k = 5
+    if kind == "limit":
+        info = G.set_polynomial(sped.POLY_LIMIT_EXP, 9)
+        apply = lambda X: oracle.poly_limit(g, X, info.scale_s, 9)
+    else:
+        c = [0.4, -0.3, 0.2, 0.1]
+        hi = oracle.gershgorin_bound(g)
+        G.set_polynomial(sped.POLY_CHEBYSHEV, 3, eps=0.1, coeffs=c, lambda_star=hi)
+        apply = lambda X: oracle.poly_chebyshev(g, X, c, 0.1, hi)
+    V0 = gen.gaussian_block(g.n, k, seed=73)
+    dY0 = gen.gaussian_block(g.n, k, seed=74)
+    dY = to_block(dY0, torch.float64)
+    dV = sped.alloc_block(g.n, k, torch.float64, DEV)
+    sped.apply_poly_backward(G, dY, dV, k)
+    torch.cuda.synchronize()
+    got = host(dV, k)
+    assert np.linalg.norm(got - apply(dY0)) <= 1e-12 * np.linalg.norm(got)
+    lhs = float(np.sum(dY0 * apply(V0)))
+    assert abs(lhs - float(np.sum(got * V0))) <= 1e-10 * abs(lhs)
