@@ -211,11 +211,53 @@ __device__ __forceinline__ void load_partial(const T *__restrict__ p, int cnt, A
 #pragma unroll
     for (int i = 0; i < E; ++i) out[i] = i < cnt ? cvt<A>(p[i]) : A(0);
 }
+// The partial store of a chunk writes the widest aligned pieces that fit (16, 8, then 4 bytes,
+// then single elements), so a BF16 row of 20 columns ends with one 8-byte store, not four 2-byte
+// ones. Chunks are 8, 16 or 32 bytes (E elements of T, naturally aligned at 16 bytes or more).
 template <typename T, int E, typename A>
 __device__ __forceinline__ void store_partial(T *p, int cnt, const A (&in)[E]) {
+    constexpr int SZ = (int)sizeof(T);
+    constexpr int NB = E * SZ;
+    if constexpr (NB != 16 && NB != 32) {
 #pragma unroll
-    for (int i = 0; i < E; ++i)
-        if (i < cnt) p[i] = from_acc<T>(in[i]);
+        for (int i = 0; i < E; ++i)
+            if (i < cnt) p[i] = from_acc<T>(in[i]);
+    } else {
+        union {
+            uint32_t w[NB / 4];
+            T e[E];
+        } u;
+#pragma unroll
+        for (int i = 0; i < E; ++i) u.e[i] = from_acc<T>(in[i]);
+        const int bytes = cnt * SZ;
+        char *q = reinterpret_cast<char *>(p);
+        int off = 0;
+        if constexpr (NB == 32) {
+            if (bytes >= 16) {
+                *reinterpret_cast<uint4 *>(q) = make_uint4(u.w[0], u.w[1], u.w[2], u.w[3]);
+                off = 16;
+            }
+        }
+        if (bytes - off >= 8) {
+            uint2 v = make_uint2(u.w[0], u.w[1]);
+            if constexpr (NB == 32)
+                if (off == 16) v = make_uint2(u.w[4], u.w[5]);
+            *reinterpret_cast<uint2 *>(q + off) = v;
+            off += 8;
+        }
+        if (bytes - off >= 4) {
+            uint32_t v = off == 0 ? u.w[0] : u.w[2];
+            if constexpr (NB == 32) {
+                if (off == 16) v = u.w[4];
+                if (off == 24) v = u.w[6];
+            }
+            *reinterpret_cast<uint32_t *>(q + off) = v;
+            off += 4;
+        }
+#pragma unroll
+        for (int i = 0; i < E; ++i)
+            if (i * SZ >= off && i < cnt) p[i] = u.e[i];
+    }
 }
 
 // Philox4x32-10 (Salmon et al., SC'11) -- device implementation of the published definition.
