@@ -189,8 +189,9 @@ __global__ void __launch_bounds__(MB_THREADS)
     k_edge_scatter(int64_t n, int k, int lanes_log2, const TX *__restrict__ X, int ldx, TY *Y,
                    int ldy, int64_t count, double coef, uint64_t seed, uint32_t step,
                    uint32_t n_edges, const int2 *__restrict__ edge_ab,
-                   const int32_t *__restrict__ edge_p, const int32_t *__restrict__ ea, const int32_t *__restrict__ eb,
-                   const float *__restrict__ w, int32_t *skipped) {
+                   const int32_t *__restrict__ edge_p, const int32_t *__restrict__ ea,
+                   const int32_t *__restrict__ eb, const float *__restrict__ w,
+                   int32_t *skipped) {
     using A = typename AccOf<TY>::type;
     constexpr int E = 16 / (int)sizeof(TY);  // elements in one 16-byte piece of a Y row
     const int C = 1 << lanes_log2;
