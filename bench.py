@@ -684,13 +684,11 @@ def measure_three_room(sped, torch, dev, stream, k=3, cap_plain=20000, cap_dilat
     return out
 
 
-def _fit_chebyshev(mu, d, k, a, b, c0):
-    """Coefficients c of M = sum_l c_l T_l(x) on [a, b] minimising the sum of the Ritz values of
-    L on span(M V), from the block moments mu_l = V^T T_l V (l <= 2d + 1): with Y = M V,
-    Y^T Y = sum c_l c_m (mu_{l+m} + mu_{|l-m|}) / 2 and Y^T L Y = sum c_l c_m V^T T_l L T_m V,
-    L = (b - a)/2 x + (a + b)/2 I, x T_m = (T_{m+1} + T_{|m-1|}) / 2. BFGS with the analytic
-    gradient of tr((Y^T Y)^-1 Y^T L Y); c is scale-free and returned with unit norm."""
-    import scipy.optimize as so
+def _cheb_quadratic_forms(mu, d, k, a, b):
+    """From the block moments mu_l = V^T T_l V (l <= 2d + 1) of the Chebyshev basis on [a, b]:
+    A[l, m] = V^T T_l T_m V = (mu_{l+m} + mu_{|l-m|}) / 2 and Bm[l, m] = V^T T_l L T_m V, with
+    L = (b - a)/2 x + (a + b)/2 I and x T_m = (T_{m+1} + T_{|m-1|}) / 2, so that for Y = M V,
+    M = sum c_l T_l: Y^T Y = sum c_l c_m A[l, m] and Y^T L Y = sum c_l c_m Bm[l, m]."""
     A = np.empty((d + 1, d + 1, k, k))
     X = np.empty_like(A)
     for l in range(d + 1):
@@ -698,7 +696,16 @@ def _fit_chebyshev(mu, d, k, a, b, c0):
             A[l, m] = 0.5 * (mu[l + m] + mu[abs(l - m)])
             X[l, m] = 0.25 * (mu[l + m + 1] + mu[abs(l - m - 1)] + mu[l + abs(m - 1)]
                               + mu[abs(l - abs(m - 1))])
-    Bm = 0.5 * (b - a) * X + 0.5 * (a + b) * A
+    return A, 0.5 * (b - a) * X + 0.5 * (a + b) * A
+
+
+def _fit_chebyshev(mu, d, k, a, b, c0):
+    """Coefficients c of M = sum_l c_l T_l(x) on [a, b] minimising the sum of the Ritz values of
+    L on span(M V), tr((Y^T Y)^-1 Y^T L Y) with Y = M V, from the block moments (see
+    _cheb_quadratic_forms). BFGS with the analytic gradient; c is scale-free and returned with
+    unit norm."""
+    import scipy.optimize as so
+    A, Bm = _cheb_quadratic_forms(mu, d, k, a, b)
 
     def f(c):
         S = np.einsum("l,m,lmij->ij", c, c, A)
