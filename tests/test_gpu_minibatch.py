@@ -276,3 +276,25 @@ def test_stratified_mean_converges_and_beats_uniform():
         assert float(np.abs(z).max()) < 6.0
         spread[mode] = float(np.mean(np.linalg.norm(outs - exact, axis=(1, 2))))
     assert spread[sped.STOCHASTIC_MINIBATCH_STRATIFIED] < spread[sped.STOCHASTIC_MINIBATCH]
+
+
+@pytest.mark.parametrize("mode", [sped.STOCHASTIC_MINIBATCH, sped.STOCHASTIC_MINIBATCH_STRATIFIED])
+def test_solve_on_minibatches_reaches_the_noise_floor(mode):
+    # mu-EG with every step's p(L) V estimated from edge minibatches (fresh draws each step):
+    # a fixed step size stops at a noise floor set by the minibatch variance; the subspace gets
+    # there from a random start
+    g = gen.sbm(2000, 4, 0.05, 0.001, seed=gen.DEFAULT_SEED)
+    G = sped.Graph.from_csr(g)
+    k = 4
+    G.set_polynomial(sped.POLY_LIMIT_EXP, 7)
+    _, Ustar = oracle.bottom_k(g, k)
+    V0 = gen.gaussian_block(g.n, k, seed=87)
+    start = oracle.principal_angle_max(Ustar, V0)
+    V = to_block(V0, torch.float64)
+    opts = sped.solve_opts(sped.MU_EG, 0.5, torch.float64, torch.float64, max_steps=80,
+                           check_every=10, tol=1e-12, refine_dtype=torch.float64, mode=mode,
+                           walkers=g.nnz // 8, seed=3)
+    _, rep = sped.solve_bottom_k(G, V, k, opts)
+    assert rep["steps"] == 80 and not rep["converged"]  # the residual never reaches 1e-12
+    ang = oracle.principal_angle_max(Ustar, host(V, k))
+    assert start > 1.0 and ang < 0.15, (start, ang)
