@@ -313,7 +313,7 @@ typedef struct {
     sped_dtype chain_t; /* storage of intermediate products                           */
     sped_dtype y_t;     /* storage of Y = M V: F32 or F64                              */
     sped_mode mode;     /* exact or stochastic p(L) V                                  */
-    int64_t walkers;    /* walks (IS / REJECT) or edges per minibatch (MINIBATCH)        */
+    int64_t walkers;    /* walks (IS / REJECT) or edges per minibatch (MINIBATCH modes)  */
     uint64_t seed;
     /* optional cudaEvent_t pair (as void*, NULL = none) recorded on the stream immediately
      * before and after the p(L) V chain, for live timing of the dominant kernel */
