@@ -6,9 +6,13 @@ solver step: p(L) V by the limit form (I - sL)^l chained in BF16 (first step rea
 master, last step writes F32), the 2k x 2k Gram [V Y]^T [V Y], the k x k FP64 mu-EG algebra and the
 N x k update. Value = algorithmic HBM bytes of the step / device time (GB/s).
 
-Also measured: the dominant kernel (one chain step) against the HBM roofline, the end-to-end
-rate through the C ABI with host buffers, time-to-bottom-k (largest principal angle <= 1e-3)
-for the dilated mixed-precision solver against the plain-L FP64 solver, and the FP64 CPU oracle.
+Also measured: the dominant kernel (one chain step) against the HBM roofline and against the
+gather-rate probe, the end-to-end rate through the C ABI with host buffers, the step replayed
+from a CUDA graph, time-to-bottom-k (largest principal angle <= 1e-3) for the dilated
+mixed-precision solver against the plain-L FP64 solver, and the FP64 CPU oracle; with the
+extended measurements (default on, `--only-extra` selects): the walk estimator, edge
+minibatches, the differentiable path, the batched solver, a permuted node order, the degree
+threshold, the 3-room grid world and fitted polynomial coefficients.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """

@@ -131,3 +131,15 @@ def test_planted_mistake_is_caught(monkeypatch):
     lam = 2 - 2 * math.cos(math.pi / g.n)
     bad = wrong_sign(g, u[:, None])[:, 0]
     assert not np.allclose(bad, lam * u, atol=1e-6)
+
+
+def test_linear_time_cycle_builder_matches_the_edge_list_builder():
+    for n in (3, 4, 5, 17):
+        a, b = gen.cycle_csr(n), gen.cycle(n)
+        assert np.array_equal(a.row_ptr, b.row_ptr) and np.array_equal(a.col_idx, b.col_idx)
+    # the hashed block is the same on the host and in torch, and exact in BF16
+    torch = pytest.importorskip("torch")
+    rows = np.array([0, 1, 7, 2 ** 27 + 3])
+    h = gen.hash_block(rows, 6)
+    assert np.array_equal(h, gen.hash_block(torch.from_numpy(rows), 6, xp=torch).numpy())
+    assert np.array_equal(h, torch.from_numpy(h).to(torch.bfloat16).double().numpy())
