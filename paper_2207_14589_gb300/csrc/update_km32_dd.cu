@@ -1,0 +1,4 @@
+// Instantiations of the solver update for rows of width 32, F64 master and F64 Y.
+#include "update_kernel.cuh"
+
+SPED_UPDATE_INSTANTIATE_PAIR(double, double, 32)
