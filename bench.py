@@ -176,15 +176,45 @@ def _job_rate(world, bytes_per_rank_step, ms_per_step):
     return world * bytes_per_rank_step / (ms_per_step * 1e-3) / 1e9
 
 
-def _principal_angle(sped, Vstar, V, k):
-    """Largest principal angle between span(V*) and span(V) from their FP64 Gram."""
+def _angle_and_delta(sped, Vstar, V, k):
+    """Largest principal angle between span(V*) and span(V), and the subspace error of Section
+    5.2, delta = 1 - tr(U* P) / k = 1 - ||Q*^T Q_V||_F^2 / k, both from their FP64 Gram."""
     G = sped.gram(Vstar, k, V, k).cpu().numpy()
     Ps, C, Pv = G[:k, :k], G[:k, k:], G[k:, k:]
     Rs = np.linalg.cholesky(Ps)
     Rv = np.linalg.cholesky(Pv)
     M = np.linalg.solve(Rs, np.linalg.solve(Rv, C.T).T)  # Q*^T Q_V
     smin = np.linalg.svd(M, compute_uv=False).min()
-    return float(math.asin(math.sqrt(max(0.0, 1.0 - min(1.0, smin) ** 2))))
+    ang = float(math.asin(math.sqrt(max(0.0, 1.0 - min(1.0, smin) ** 2))))
+    return ang, float(max(0.0, 1.0 - np.sum(M * M) / k))
+
+
+def _principal_angle(sped, Vstar, V, k):
+    """Largest principal angle between span(V*) and span(V) from their FP64 Gram."""
+    return _angle_and_delta(sped, Vstar, V, k)[0]
+
+
+def certify_reference(g, Vs, k):
+    """Davis-Kahan certificate of a reference subspace, computed by the FP64 oracle on the host
+    (Section 8 of the design: the reference of time-to-bottom-k must not rest on the GPU path
+    alone). Rayleigh-Ritz of L on span(Vs) (kp >= k + 1 columns) gives Ritz pairs
+    (theta_i, u_i); the residual block R = L U_k - U_k Theta_k of the first k Ritz vectors and
+    the gap delta = theta_{k+1} - theta_k to the first guard Ritz value bound the largest
+    principal angle between span(U_k) and the bottom-k eigenvectors of L by
+    sin(theta_max) <= ||R||_2 / delta (sin-theta theorem; delta stands in for
+    lambda_{k+1} - theta_k, as the guard vectors estimate lambda_{k+1}). The reference the
+    arms are graded against is thereby checked by code that shares nothing with the GPU."""
+    import oracle
+    Vh = np.ascontiguousarray(Vs, dtype=np.float64)
+    theta, W = oracle.rayleigh_ritz(g, Vh)
+    U = Vh @ W[:, :k]
+    R = oracle.laplacian_apply(g, U) - U * theta[:k]
+    rnorm = float(math.sqrt(max(0.0, np.linalg.eigvalsh(R.T @ R).max())))
+    gap = float(theta[k] - theta[k - 1])
+    return {"by": "oracle (FP64 CPU Rayleigh-Ritz and residual of the GPU reference block)",
+            "ritz_values": [float(x) for x in theta[:k + 1]],
+            "residual_2norm": rnorm, "gap_theta_k1_minus_theta_k": gap,
+            "davis_kahan_sin_theta_bound": rnorm / gap if gap > 0 else None}
 
 
 def _eigen_errors(sped, torch, G, V, k, master, Vref, theta_ref, dense):
@@ -219,6 +249,13 @@ TTK_ARMS = {
     # Ritz values): damps the unwanted part of the spectrum, grows fastest below it
     "chebyshev_filter_mixed_oja": dict(poly=("cheb", 15), solver="oja", eta=0.0,
                                        chain=("bf16", "f32"), master="f32", cap=200),
+    # the same solvers in FP64 on the dilated operator, then on the plain reversed Laplacian
+    # lambda* I - L (Eq. reveig): same-solver ratios separate the dilation's gain from the
+    # choice of solver and from the precision
+    "dilated_fp64_oja": dict(poly=("limit", 15), solver="oja", eta=0.0,
+                             chain=("f64",), master="f64", cap=200),
+    "plain_fp64_oja": dict(poly=("shift", 1), solver="oja", eta=0.0,
+                           chain=("f64",), master="f64", cap=3000),
     "plain_fp64_mu_eg": dict(poly=("shift", 1), solver="mu_eg", eta=None,
                              chain=("f64",), master="f64", cap=3000),
     "plain_fp32_mu_eg": dict(poly=("shift", 1), solver="mu_eg", eta=None,
@@ -226,7 +263,8 @@ TTK_ARMS = {
 }
 
 
-def time_to_bottom_k(sped, torch, g, k, dev, stream, ell_ref, ref_steps=14, seed=SEED):
+def time_to_bottom_k(sped, torch, g, k, dev, stream, ell_ref, ref_steps=14, seed=SEED,
+                     certify=True, kp=None, arms=None):
     """Time to reach a largest principal angle <= 1e-3 to the bottom-k subspace, per arm.
 
     Reference subspace: FP64 subspace iteration on the dilated operator (l = ell_ref) run far
@@ -240,7 +278,7 @@ def time_to_bottom_k(sped, torch, g, k, dev, stream, ell_ref, ref_steps=14, seed
     V0 = torch.from_numpy(gen.gaussian_block(n, k, seed=seed)).to(dev)
     G.set_polynomial(sped.POLY_LIMIT_EXP, ell_ref)
     # reference: k + 4 vectors (the extra ones speed it up and estimate lambda_{k+1})
-    kp = k + 4
+    kp = kp or k + 4
     Vs = sped.alloc_block(n, kp, torch.float64, dev)
     Vs[:, :kp] = torch.from_numpy(gen.gaussian_block(n, kp, seed=seed + 31)).to(dev)
     Vs[:, :k] = V0
@@ -262,6 +300,9 @@ def time_to_bottom_k(sped, torch, g, k, dev, stream, ell_ref, ref_steps=14, seed
                          "vectors": kp, "ritz_value_k_plus_1": float(theta_all[k]),
                          "invariant_subspace_residual": ref_residual,
                          "ritz_values": [float(x) for x in theta_ref]}}
+    if certify:
+        out["reference"]["certificate"] = certify_reference(
+            g, Vs[:, :kp].cpu().numpy(), k)
     dense = None
     if n <= 4000:  # small graph: also against the dense FP64 eigendecomposition of L
         Ld = np.zeros((n, n))
@@ -273,6 +314,8 @@ def time_to_bottom_k(sped, torch, g, k, dev, stream, ell_ref, ref_steps=14, seed
         out["reference"]["dense_eigenvalue_error_max"] = float(np.abs(theta_ref - lam[:k]).max())
     del scr
     for name, a in TTK_ARMS.items():
+        if arms is not None and name not in arms:
+            continue
         if a["poly"][0] == "limit":
             info = G.set_polynomial(sped.POLY_LIMIT_EXP, a["poly"][1])
         elif a["poly"][0] == "cheb":
@@ -290,7 +333,7 @@ def time_to_bottom_k(sped, torch, g, k, dev, stream, ell_ref, ref_steps=14, seed
                           dtype=torch.uint8, device=dev)
         V = sped.alloc_block(n, k, master, dev)
         V[:, :k] = V0.to(master)
-        phase, hist, schedule, steps, ang = 0, [], [], None, None
+        phase, hist, schedule, steps, ang, delta = 0, [], [], None, None, None
         for t in range(1, a["cap"] + 1):
             c = a["chain"][phase]
             sped.eig_step(G, V, k, opts[c], stats=stats, scratch=scr)
@@ -301,11 +344,12 @@ def time_to_bottom_k(sped, torch, g, k, dev, stream, ell_ref, ref_steps=14, seed
                 if res <= 3e-3 or (len(hist) >= 4 and res > 0.9 * hist[-4]):
                     phase += 1
             if t <= 400 or t % 10 == 0:
-                ang = _principal_angle(sped, Vs, V, k)
+                ang, delta = _angle_and_delta(sped, Vs, V, k)
                 if ang <= 1e-3:
                     steps = t
                     break
-        rec = {"steps": steps, "angle": ang, "degree": info.degree, "eta": eta,
+        rec = {"steps": steps, "angle": ang, "subspace_error_delta": delta,
+               "degree": info.degree, "eta": eta,
                "spmm": None if steps is None else steps * info.degree,
                "chain_schedule": {c: schedule.count(c) for c in a["chain"]}}
         if steps is not None:
@@ -322,15 +366,77 @@ def time_to_bottom_k(sped, torch, g, k, dev, stream, ell_ref, ref_steps=14, seed
             rec.update(_eigen_errors(sped, torch, G, V, k, master, Vs, theta_ref, dense))
         out[name] = rec
         del scr, V
-    p = out["plain_fp64_mu_eg"].get("ms")
-    best = min([out[a].get("ms") or math.inf for a in ("dilated_mixed_mu_eg", "dilated_mixed_oja")])
-    if p and best < math.inf:
-        out["speedup_best_dilated_vs_plain_fp64"] = p / best
-    if p and out["chebyshev_filter_mixed_oja"].get("ms"):
-        out["speedup_chebyshev_filter_vs_plain_fp64"] = p / out["chebyshev_filter_mixed_oja"]["ms"]
-    if p and out["dilated_mixed_mu_eg"].get("ms"):
-        out["speedup_mu_eg_dilated_vs_plain_fp64"] = p / out["dilated_mixed_mu_eg"]["ms"]
+    out.update(ttk_ratios(out))
     return out
+
+
+def ttk_ratios(out):
+    """Speed-ups from the arms' device times: the same solver on the plain reversed Laplacian
+    (FP64) over the dilated operator (mixed precision, and FP64 to isolate the dilation), and the
+    best dilated arm over the best plain FP64 arm."""
+    ms = lambda a: (out.get(a) or {}).get("ms")
+    r = {}
+    for key, plain, dil in (("same_solver_speedup_oja", "plain_fp64_oja", "dilated_mixed_oja"),
+                            ("same_solver_speedup_mu_eg", "plain_fp64_mu_eg",
+                             "dilated_mixed_mu_eg"),
+                            ("dilation_only_speedup_oja_fp64", "plain_fp64_oja",
+                             "dilated_fp64_oja")):
+        if ms(plain) and ms(dil):
+            r[key] = ms(plain) / ms(dil)
+    plains = [ms(a) for a in ("plain_fp64_oja", "plain_fp64_mu_eg") if ms(a)]
+    dils = [ms(a) for a in ("dilated_mixed_oja", "dilated_mixed_mu_eg") if ms(a)]
+    if plains and dils:
+        r["speedup_best_dilated_vs_plain_fp64"] = min(plains) / min(dils)
+    if ms("plain_fp64_mu_eg") and ms("chebyshev_filter_mixed_oja"):
+        r["speedup_chebyshev_filter_vs_plain_fp64"] = \
+            min(plains) / ms("chebyshev_filter_mixed_oja")
+    return r
+
+
+def pick_graded_k(theta, k_min, rel_gap=0.05):
+    """The smallest k >= k_min whose Ritz gap theta_{k+1} - theta_k is at least rel_gap of
+    theta_{k+1} (a gap the solvers resolve in tens of steps), else the k with the largest
+    relative gap (theta ascending, the last few values left as guards)."""
+    theta = np.asarray(theta, dtype=np.float64)
+    last = len(theta) - 4
+    rel = [(theta[j] - theta[j - 1]) / max(abs(theta[j]), 1e-300) for j in range(1, len(theta))]
+    for kk in range(k_min, last + 1):
+        if rel[kk - 1] >= rel_gap:
+            return kk, rel[kk - 1]
+    kk = int(np.argmax(rel[k_min - 1:last])) + k_min
+    return kk, rel[kk - 1]
+
+
+def ttk_benchmark_graph(sped, torch, g, G, dev, stream, k_min, ell, kp=32, probe_steps=30,
+                        min_rel_gap=0.02):
+    """Time-to-bottom-k on the benchmark SBM itself. Its bottom-20 sits inside a cluster of
+    block modes and modes localized at low-degree nodes with no clear gap after the 20th, so the
+    angle is graded at the nearest k >= 20 with a clear gap: an FP64 subspace iteration with kp
+    vectors on the dilated operator gives the Ritz values, pick_graded_k picks k (leaving four
+    guard vectors for the reference), and the mixed-precision dilated arms race the plain-L
+    FP64 arms at that k. When no gap of at least min_rel_gap exists below kp - 4 (the solver
+    path takes k <= 32), the probe is reported and nothing is graded."""
+    res, _ = spectrum_probe(sped, torch, G, g.n, dev, kp=kp, steps=(probe_steps,))
+    theta = res[probe_steps]["ritz"]
+    kk, gap = pick_graded_k(theta, k_min)
+    name = f"sbm_n{g.n}_b{WORKLOAD['blocks']}_deg16_benchmark_graph"
+    G.set_polynomial(sped.POLY_LIMIT_EXP, ell)
+    if gap < min_rel_gap:
+        return {name: {"graded": False, "probe_ritz_values": theta,
+                       "probe_max_residual": res[probe_steps]["max_residual"],
+                       "why": f"no relative Ritz gap >= {min_rel_gap} for k in [{k_min}, "
+                              f"{kp - 4}] (largest {gap:.3g} at k = {kk}); the solver path "
+                              f"takes k <= 32"}}
+    r = time_to_bottom_k(sped, torch, g, kk, dev, stream, ell, ref_steps=40, kp=min(kk + 4, 32),
+                         arms=("dilated_mixed_oja", "dilated_mixed_mu_eg", "dilated_fp64_oja",
+                               "plain_fp64_oja", "plain_fp64_mu_eg"))
+    G.set_polynomial(sped.POLY_LIMIT_EXP, ell)
+    r["k_graded"] = kk
+    r["why_k"] = (f"bottom-{k_min} is not separated from the next Ritz values; k = {kk} is the "
+                  f"nearest with a relative gap {gap:.3g} (probe: {kp} FP64 vectors, "
+                  f"{probe_steps} steps)")
+    r["probe_ritz_values"] = theta
+    return {name: r}
 
 
 def ritz_spectrum(sped, torch, G, V, k):
@@ -978,6 +1084,9 @@ def run_ours(args, rank, world, local_rank):
     achieved = per_launch_bytes / (launch_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": _ncu_traffic(),
+                "traffic_source": "from profile: ncu dram bytes per launch in "
+                                  "profiles/step_rowgroup_bf16_sbm1e6_k20.md, taken on this "
+                                  "kernel source (null when the source changed since)",
                 "kernel": "k_step_rowgroup (chain step, bf16 storage, f32 accumulate)",
                 "per_launch_bytes": per_launch_bytes, "launch_us": launch_ms * 1e3,
                 "peak_kind": f"{peak_kind} (copy, burst)"}
@@ -1121,13 +1230,15 @@ def run_ours(args, rank, world, local_rank):
             r = time_to_bottom_k(sped, torch, gs, 4, dev, stream, 45, seed=sd)
             per_seed[sd] = {a: {"steps": r[a]["steps"], "ms": r[a].get("ms")}
                             for a in TTK_ARMS}
-            per_seed[sd]["speedup_best_dilated_vs_plain_fp64"] = \
-                r.get("speedup_best_dilated_vs_plain_fp64")
+            per_seed[sd].update(ttk_ratios(r))
         extra["time_to_bottom_k"]["sbm_n2000_b4_k4_seeds_0_1_2"] = per_seed
+        # the benchmark graph itself, graded at the nearest k >= 20 whose Ritz gap is clear
+        extra["time_to_bottom_k"].update(ttk_benchmark_graph(sped, torch, g, G, dev, stream,
+                                                             k, ell))
     clocks = clk.summary()
     if rank != 0:
         return
-    line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": K,
+    full = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": K,
             "warmup": W, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16", "data": "synthetic", "config": _config(g),
             "roofline": roofline, "e2e": e2e, "clocks": clocks,
@@ -1136,10 +1247,83 @@ def run_ours(args, rank, world, local_rank):
             "cuda_graph_replay": graph_rec,
             "gather_ceiling": gather,
             "step_bytes": step_b}
-    line.update(extra)
+    full.update(extra)
     if not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(g)
-    print(json.dumps(line), flush=True)
+        full["cpu_baseline"] = cpu_baseline(g)
+    emit(full, args.extras_out)
+
+
+# keys of the headline line; everything else goes to the extra lines (and the extras file)
+HEADLINE_KEYS = ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                 "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+                 "roofline", "e2e", "cpu_baseline", "clocks", "gpu_launches")
+
+
+def _round(x, digits=4):
+    """Floats to `digits` significant digits, recursively (keeps the headline short)."""
+    if isinstance(x, float):
+        return float(f"{x:.{digits}g}") if math.isfinite(x) else None
+    if isinstance(x, dict):
+        return {k: _round(v, digits) for k, v in x.items()}
+    if isinstance(x, (list, tuple)):
+        return [_round(v, digits) for v in x]
+    return x
+
+
+def ttk_summary(ttk):
+    """Compact time-to-bottom-k figures per graph: [steps, ms] of every arm, the same-solver
+    ratios (plain-L time over dilated time, same solver), and the reference's certificate."""
+    out = {}
+    for gname, r in ttk.items():
+        if not isinstance(r, dict) or "reference" not in r:
+            continue
+        s = {arm: [r[arm].get("steps"), r[arm].get("ms")] for arm in TTK_ARMS if arm in r}
+        for key in ("same_solver_speedup_oja", "same_solver_speedup_mu_eg",
+                    "speedup_best_dilated_vs_plain_fp64"):
+            if r.get(key) is not None:
+                s[key] = r[key]
+        cert = r["reference"].get("certificate")
+        if cert:
+            s["reference_sin_theta_bound"] = cert.get("davis_kahan_sin_theta_bound")
+        if r.get("k_graded") is not None:
+            s["k_graded"] = r["k_graded"]
+        out[gname] = s
+    return out
+
+
+def headline(full):
+    """The one JSON line the benchmark ends with: the contract's keys (with the long
+    descriptions shortened) plus the time-to-bottom-k summary; a few KB at most."""
+    line = {k: full[k] for k in HEADLINE_KEYS if k in full}
+    rf = dict(line.get("roofline") or {})
+    line["roofline"] = {k: rf[k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic",
+                                           "traffic_source", "kernel", "per_launch_bytes",
+                                           "launch_us", "peak_kind") if k in rf}
+    cb = full.get("cpu_baseline")
+    if cb:
+        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")
+                                if k in cb}
+    if "e2e" in line:
+        line["e2e"] = {k: line["e2e"][k] for k in ("value", "unit", "h2d_bytes_per_step",
+                                                   "d2h_bytes_per_step", "ms_per_step")
+                       if k in line["e2e"]}
+    if "time_to_bottom_k" in full:
+        line["time_to_bottom_k"] = ttk_summary(full["time_to_bottom_k"])
+    return _round(line)
+
+
+def emit(full, extras_out=None):
+    """Print every extended measurement as its own JSON line ({"extra": name, "result": ...}),
+    write all of them to `extras_out` when given, and end with the headline line."""
+    rest = {k: v for k, v in full.items() if k not in HEADLINE_KEYS}
+    for name, val in rest.items():
+        print(json.dumps({"extra": name, "result": _round(val, 6)}), flush=True)
+    if extras_out:
+        d = os.path.dirname(os.path.abspath(extras_out))
+        os.makedirs(d, exist_ok=True)
+        with open(extras_out, "w") as f:
+            json.dump(full, f, indent=1)
+    print(json.dumps(headline(full)), flush=True)
 
 
 def ctypes_ptr(event):
@@ -1169,6 +1353,8 @@ def main():
                     help="nodes of the Chung-Lu graph for --power-law")
     ap.add_argument("--target-nnz", type=float, default=None,
                     help="scale the Chung-Lu expected degrees to this many stored entries")
+    ap.add_argument("--extras-out", default=None,
+                    help="also write every measurement (headline and extras) to this JSON file")
     ap.add_argument("--spectrum", action="store_true",
                     help="print the bottom of the workload's spectrum and exit")
     args = ap.parse_args()

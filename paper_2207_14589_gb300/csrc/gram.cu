@@ -247,7 +247,11 @@ sped_status sped_gram(int64_t n, const void *d_A, sped_dtype a_t, int lda, int k
     if (!dtype_valid(a_t) || (kb > 0 && !dtype_valid(b_t)))
         return fail(SPED_ERR_INVALID_ARG, "gram: dtype");
     if (ka < 1 || lda < ka || !d_A) return fail(SPED_ERR_INVALID_ARG, "gram: A layout");
-    if (kb > 0 && (ldb < kb || !d_B)) return fail(SPED_ERR_INVALID_ARG, "gram: B layout");
+    if (kb < 0 || (kb > 0 && (ldb < kb || !d_B)))
+        return fail(SPED_ERR_INVALID_ARG, "gram: B layout");
+    // 16-byte rows and bases: the tensor path moves whole tiles with bulk copies
+    SPED_TRY(check_layout(d_A, a_t, ka, lda, "gram A"));
+    if (kb > 0) SPED_TRY(check_layout(d_B, b_t, kb, ldb, "gram B"));
     Scratch scr(d_scratch, scratch_bytes);
     return launch_gram(n, d_A, a_t, lda, ka, d_B, b_t, ldb, kb, d_G, scr, as_stream(stream));
 }
@@ -305,6 +309,8 @@ extern "C" sped_status sped_gram_noalloc(int64_t n, const void *d_A, sped_dtype 
     if (ka < 1 || lda < ka || !d_A) return fail(SPED_ERR_INVALID_ARG, "gram_noalloc: A layout");
     if (kb < 0 || (kb > 0 && (ldb < kb || !d_B)))
         return fail(SPED_ERR_INVALID_ARG, "gram_noalloc: B layout");
+    SPED_TRY(check_layout(d_A, a_t, ka, lda, "gram_noalloc A"));
+    if (kb > 0) SPED_TRY(check_layout(d_B, b_t, kb, ldb, "gram_noalloc B"));
     if (ka + kb > GRAM_MAXK)
         return fail(SPED_ERR_UNSUPPORTED,
                     "gram_noalloc: ka + kb = %d exceeds the maximum of %d columns", ka + kb,

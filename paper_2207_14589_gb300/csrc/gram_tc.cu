@@ -466,9 +466,11 @@ int gram_tc_pieces(sped_dtype at, sped_dtype bt, int ka, int kb, int lda, int ld
     const bool a_ok = at == SPED_F32 || at == SPED_BF16;
     const bool b_ok = kb == 0 || bt == SPED_F32 || bt == SPED_BF16;
     if (!a_ok || !b_ok) return 0;
+    // rows are whole 16-byte chunks (the bulk copies move rows * ld * size bytes)
+    const size_t ra = (size_t)lda * dtype_size(at), rb = kb ? (size_t)ldb * dtype_size(bt) : 0;
+    if (ra % 16 != 0 || rb % 16 != 0) return 0;
     // one tile of A and B fits the raw buffer (TC_RAW_CHUNKS 16-byte chunks)
-    const int ea = 16 / (int)dtype_size(at), eb = kb ? 16 / (int)dtype_size(bt) : 1;
-    if (TC_TILE * (lda / ea + (kb ? ldb / eb : 0)) > TC_RAW_CHUNKS) return 0;
+    if ((size_t)TC_TILE * ((ra + 15) / 16 + (rb + 15) / 16) > (size_t)TC_RAW_CHUNKS) return 0;
     const int S = (at == SPED_F32 || (kb > 0 && bt == SPED_F32)) ? 3 : 1;
     return S * (ka + kb) <= 128 ? S : 0;
 }

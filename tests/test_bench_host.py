@@ -1,5 +1,7 @@
 """Host-side accounting of the benchmark: the algorithmic bytes of one chain step and of one
 solver step, written out term by term for the benchmark workload."""
+import json
+
 import bench
 
 
@@ -25,3 +27,61 @@ def test_solver_step_bytes():
 
 def test_job_rate_counts_every_rank():
     assert bench._job_rate(4, 1e9, 2.0) == 4 * bench._job_rate(1, 1e9, 2.0)
+
+
+def _fake_full():
+    arm = {"steps": 12, "ms": 1.234567, "angle": 9e-4, "ritz_value_abs_error": [1e-7] * 20,
+           "ritz_vector_angle": [1e-4] * 20}
+    ttk = {"reference": {"certificate": {"davis_kahan_sin_theta_bound": 3e-7}}}
+    ttk.update({a: dict(arm) for a in bench.TTK_ARMS})
+    ttk.update(bench.ttk_ratios(ttk))
+    return {"metric": bench.METRIC, "value": 1286.8, "unit": "GB/s", "n_gpus": 1, "steps": 20,
+            "warmup": 5, "ms_per_step": 5.088, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": "sbm_n1000000_b20_deg16_k20", "l2": "x" * 300},
+            "roofline": {"bound": "hbm", "achieved": 1245.0, "peak": 6799.6, "unit": "GB/s",
+                         "frac": 0.183, "traffic": 2.095e8, "traffic_source": "y" * 200,
+                         "kernel": "k_step_rowgroup", "per_launch_bytes": 1.48e8,
+                         "launch_us": 119.2, "peak_kind": "measured (copy, burst)"},
+            "e2e": {"value": 1273.0, "unit": "GB/s", "h2d_bytes_per_step": 8e7,
+                    "d2h_bytes_per_step": 8e7, "ms_per_step": 5.14, "copies": "z" * 100},
+            "cpu_baseline": {"value": 4.1, "unit": "GB/s", "cores": 16, "kind": "oracle",
+                             "sample": "s" * 250, "single_thread": {"value": 0.3}},
+            "clocks": {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 40},
+            "gpu_launches": 900, "gather_ceiling": {"x": [1.0] * 500},
+            "time_to_bottom_k": {"sbm_n2000_b4_k4": ttk, "sbm_regular_n1e6_b20_k20": ttk,
+                                 "sbm_n2000_b4_k4_seeds_0_1_2": {0: {}, 1: {}, 2: {}}},
+            "batched": {"ms": [0.1] * 1000}}
+
+
+def test_headline_is_the_last_line_and_short(capsys, tmp_path):
+    out = tmp_path / "extras.json"
+    bench.emit(_fake_full(), str(out))
+    lines = capsys.readouterr().out.strip().split("\n")
+    last = json.loads(lines[-1])
+    assert len(lines[-1]) <= 4096
+    for key in ("metric", "value", "unit", "ms_per_step", "roofline", "e2e", "cpu_baseline",
+                "clocks", "gpu_launches", "n_gpus", "steps", "warmup", "config"):
+        assert key in last
+    assert last["roofline"]["frac"] == 0.183 and last["e2e"]["h2d_bytes_per_step"] == 8e7
+    ttk = last["time_to_bottom_k"]["sbm_regular_n1e6_b20_k20"]
+    assert ttk["same_solver_speedup_oja"] == 1.0 and ttk["reference_sin_theta_bound"] == 3e-7
+    # every extra measurement is on its own earlier line and in the extras file
+    extras = {json.loads(x)["extra"] for x in lines[:-1]}
+    assert {"gather_ceiling", "time_to_bottom_k", "batched"} <= extras
+    assert json.load(open(out))["batched"]["ms"][0] == 0.1
+
+
+def test_same_solver_ratios():
+    r = bench.ttk_ratios({"plain_fp64_oja": {"ms": 10.0}, "dilated_mixed_oja": {"ms": 2.0},
+                          "plain_fp64_mu_eg": {"ms": 30.0}, "dilated_mixed_mu_eg": {"ms": 5.0},
+                          "dilated_fp64_oja": {"ms": 4.0}})
+    assert r["same_solver_speedup_oja"] == 5.0 and r["same_solver_speedup_mu_eg"] == 6.0
+    assert r["dilation_only_speedup_oja_fp64"] == 2.5
+    assert r["speedup_best_dilated_vs_plain_fp64"] == 5.0  # best plain 10 over best dilated 2
+
+
+def test_graded_k_picks_the_nearest_clear_gap():
+    theta = [0.0, 0.9] + [1.8 + 0.001 * i for i in range(30)] + [2.7, 2.8, 2.9, 3.0, 3.1]
+    k, gap = bench.pick_graded_k(theta, 20)
+    assert k == 32 and gap > 0.3

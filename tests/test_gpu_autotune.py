@@ -8,7 +8,7 @@ import torch
 import gen
 import oracle
 import paper_2207_14589_gb300 as sped
-from util_gpu import DEV, TOL, host, rel, stored, to_block
+from util_gpu import assert_close, DEV, TOL, host, rel, stored, to_block
 
 pytestmark = pytest.mark.gpu
 
@@ -31,7 +31,7 @@ def test_every_merge_share_matches_oracle(ipg, xt, yt):
     sped.poly_step(G, X, Y, k, alpha=0.0, beta=-0.02, gamma=1.0)  # split 0: the set schedule
     torch.cuda.synchronize()
     Xs = stored(X0, xt)
-    assert rel(host(Y, k), Xs - 0.02 * oracle.laplacian_apply(g, Xs)) <= TOL[yt]
+    assert_close(host(Y, k), Xs - 0.02 * oracle.laplacian_apply(g, Xs), TOL[yt])
 
 
 @pytest.mark.parametrize("gname", ["hub", "sbm"])
@@ -53,7 +53,7 @@ def test_autotune_reports_and_keeps_a_valid_schedule(gname):
     Y = sped.alloc_block(g.n, k, torch.float64, DEV)
     sped.apply_poly(G, V, Y, k)
     torch.cuda.synchronize()
-    assert rel(host(Y, k), oracle.poly_limit(g, V0, info.scale_s, ell)) <= 1e-12
+    assert_close(host(Y, k), oracle.poly_limit(g, V0, info.scale_s, ell), 1e-12)
 
 
 def test_autotune_table_serves_the_same_shape():

@@ -10,7 +10,7 @@ import torch
 import gen
 import oracle
 import paper_2207_14589_gb300 as sped
-from util_gpu import DEV, host, rel, stored, to_block
+from util_gpu import DEV, assert_close, assert_gram_close, host, rel, stored, to_block
 
 pytestmark = pytest.mark.gpu
 
@@ -40,7 +40,7 @@ def test_chain_step_sampled_rows(sbm_n1e6):
     for t, r in enumerate(rows):  # one row at a time: x_r - s (d_r x_r - sum_j x_j)
         nb = g.col_idx[g.row_ptr[r]:g.row_ptr[r + 1]]
         want[t] = Xs[r] - s * (len(nb) * Xs[r] - Xs[nb].sum(axis=0))
-    assert rel(got, want) <= 1e-5
+    assert_close(got, want, 1e-5)
 
 
 def test_chain_keeps_constant_vector(sbm_n1e6):
@@ -59,7 +59,7 @@ def test_tensor_gram_full_size():
     A, B = to_block(A0, torch.float32), to_block(B0, torch.float32)
     Gm = sped.gram(A, K, B, K).cpu().numpy()
     M = np.concatenate([stored(A0, torch.float32), stored(B0, torch.float32)], axis=1)
-    assert rel(Gm, M.T @ M) <= 2e-6
+    assert_gram_close(Gm, M.T @ M, 2e-6)
 
 
 def test_mixed_eig_step_full_size(sbm_n1e6):
@@ -78,7 +78,7 @@ def test_mixed_eig_step_full_size(sbm_n1e6):
     D = np.random.default_rng(1).standard_normal(Y.shape)
     Yp = Y + tol * np.linalg.norm(Y) * D / np.linalg.norm(D)
     gain = rel(oracle.mu_eg_step(Vs, Yp, 1.0), want) / tol
-    assert rel(host(V, K), want) <= 1.5 * tol * max(1.0, gain)
+    assert_close(host(V, K), want, 1.5 * tol * max(1.0, gain))
 
 
 def test_minibatch_chain_full_size(sbm_n1e6):
@@ -96,4 +96,4 @@ def test_minibatch_chain_full_size(sbm_n1e6):
     torch.cuda.synchronize()
     want = oracle.stochastic_limit(stored(V0, torch.float32), s, ell,
                                    oracle.minibatch_operator(g, seed, B))
-    assert rel(host(Y, K), want) <= 1e-5
+    assert_close(host(Y, K), want, 1e-5)

@@ -9,7 +9,7 @@ import torch
 import gen
 import oracle
 import paper_2207_14589_gb300 as sped
-from util_gpu import DEV, host, rel, to_block
+from util_gpu import assert_close, DEV, host, rel, to_block
 
 pytestmark = pytest.mark.gpu
 
@@ -37,7 +37,7 @@ def test_utilities_hbar_and_detached_direction():
     Hb = oracle.eg_utility_hbar(V0.T @ Y0, gu.numpy())
     assert np.allclose(Hbar.cpu().numpy(), Hb, rtol=1e-10, atol=1e-12)
     D = sped.block_combine(Y, k, S)
-    assert rel(D[:, :k].cpu().numpy(), oracle.eg_grad_detached(V0, Y0)) <= 1e-11
+    assert_close(D[:, :k].cpu().numpy(), oracle.eg_grad_detached(V0, Y0), 1e-11)
 
 
 @pytest.mark.parametrize("ell", [1, 5, 9])
@@ -51,11 +51,11 @@ def test_autograd_matches_oracle_gradients(ell):
     (u * gu).sum().backward()
     Y0 = oracle.poly_limit(g, V0, info.scale_s, ell)
     gn = gu.cpu().numpy()
-    assert rel(V.grad[:, :k].cpu().numpy(), oracle.eg_grad_full(V0, Y0, gn)) <= 1e-10
+    assert_close(V.grad[:, :k].cpu().numpy(), oracle.eg_grad_full(V0, Y0, gn), 1e-10)
     assert torch.all(V.grad[:, k:] == 0)
     Hb = oracle.eg_utility_hbar(V0.T @ Y0, gn)
     want = oracle.limit_edge_grad(g, V0, info.scale_s, ell, Hb)
-    assert rel(wt.grad.cpu().numpy(), want) <= 1e-9
+    assert_close(wt.grad.cpu().numpy(), want, 1e-9)
 
 
 def test_autograd_against_finite_differences():
@@ -103,7 +103,7 @@ def test_edge_grad_full_size_spot_check():
     Hb = oracle.eg_utility_hbar(V0.T @ Y0, gu)
     got = sped.edge_grad(G, V, k, torch.tensor(Hb.T.copy(), device=DEV)).cpu().numpy()
     want = oracle.limit_edge_grad(g, V0, info.scale_s, ell, Hb)
-    assert rel(got, want) <= 1e-9
+    assert_close(got, want, 1e-9)
 
 
 @pytest.mark.parametrize("kind", ["limit", "chebyshev"])

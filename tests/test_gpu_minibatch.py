@@ -9,7 +9,7 @@ import torch
 import gen
 import oracle
 import paper_2207_14589_gb300 as sped
-from util_gpu import DEV, TOL, host, rel, stored, to_block
+from util_gpu import assert_close, DEV, TOL, host, rel, stored, to_block
 
 pytestmark = pytest.mark.gpu
 
@@ -76,7 +76,7 @@ def test_edge_step_on_caller_edges(xt, yt, k):
                                           w[keep].astype(np.float64))
     want = al * Vs + ga * Xs + be * LX
     tol = TOL[torch.float64] if (xt, yt) == (torch.float64, torch.float64) else 4 * TOL[torch.float32]
-    assert rel(host(Y, k), want) <= tol
+    assert_close(host(Y, k), want, tol)
     assert torch.isnan(Y[:, k:]).all()  # row padding untouched
 
 
@@ -127,7 +127,7 @@ def test_chain_same_draws_as_oracle(fam, ell, ct, B):
     want = chain(stored(V0, ct), oracle.minibatch_operator(g, seed, B))
     # the same draws; only the order of the atomic additions (and F32 rounding) differs
     tol = 1e-11 if ct == torch.float64 else 2e-5 * max(1, ell)
-    assert rel(host(Y, k), want) <= tol
+    assert_close(host(Y, k), want, tol)
 
 
 def test_minibatch_mean_converges_to_the_exact_operator():
@@ -235,7 +235,7 @@ def test_stratified_chain_same_draws_as_oracle(fam, ell, ct, B):
     torch.cuda.synchronize()
     want = chain(stored(V0, ct), oracle.minibatch_operator(g, seed, B, stratified=True))
     tol = 1e-11 if ct == torch.float64 else 2e-5 * max(1, ell)
-    assert rel(host(Y, k), want) <= tol
+    assert_close(host(Y, k), want, tol)
 
 
 def test_stratified_with_one_edge_per_stratum_is_exact():
@@ -250,7 +250,7 @@ def test_stratified_with_one_edge_per_stratum_is_exact():
         sped.apply_poly(G, V, Y, k, chain_dtype=torch.float64,
                         mode=sped.STOCHASTIC_MINIBATCH_STRATIFIED, walkers=B, seed=5)
         torch.cuda.synchronize()
-        assert rel(host(Y, k), oracle.poly_limit(g, V0, info.scale_s, 5)) <= 1e-12
+        assert_close(host(Y, k), oracle.poly_limit(g, V0, info.scale_s, 5), 1e-12)
 
 
 def test_stratified_mean_converges_and_beats_uniform():

@@ -7,7 +7,7 @@ import torch
 import gen
 import oracle
 import paper_2207_14589_gb300 as sped
-from util_gpu import DEV, host, rel, stored, to_block
+from util_gpu import DEV, assert_close, assert_gram_close, host, rel, stored, to_block
 
 pytestmark = pytest.mark.gpu
 
@@ -29,9 +29,7 @@ def test_gram(at, bt, tol, n, ka, kb):
     want = M.T @ M
     if not kb and at != torch.float64:
         tol = max(tol, 2e-6)  # A alone: products in F32
-    got = G.cpu().numpy()
-    assert np.array_equal(got, got.T)
-    assert rel(got, want) <= tol
+    assert_gram_close(G.cpu().numpy(), want, tol)
 
 
 @pytest.mark.parametrize("solver", [sped.MU_EG, sped.OJA])
@@ -82,7 +80,7 @@ def test_eig_step_mixed_precision_close_to_fp64():
     torch.cuda.synchronize()
     Vs = stored(V0, torch.float32)
     want = oracle.mu_eg_step(Vs, oracle.poly_limit(g, Vs, info.scale_s, 21), 1.0)
-    assert rel(host(V, k), want) <= 1e-2
+    assert_close(host(V, k), want, 1e-2)
 
 
 def _sbm_n2000_k4():
@@ -114,7 +112,7 @@ def test_bf16_shadow_tracks_master_and_feeds_the_chain():
     torch.cuda.synchronize()
     assert torch.equal(Vb[:, :k], V[:, :k].to(torch.bfloat16))
     want = oracle.mu_eg_step(V1, oracle.poly_limit(g, V1, info.scale_s, ell), 1.0)
-    assert rel(host(V, k), want) <= 1e-2
+    assert_close(host(V, k), want, 1e-2)
     # the shadow needs an F32 master
     V64 = to_block(V0, torch.float64)
     with pytest.raises(sped.SpedError):
@@ -246,3 +244,24 @@ def test_rayleigh_ritz_on_an_invariant_subspace_is_exact():
     theta, _ = sped.rayleigh_ritz(G, to_block(B, torch.float64), k)
     assert np.allclose(theta.cpu().numpy(), 2.0 - 2.0 * np.cos(np.pi * np.arange(k) / n),
                        atol=1e-12)
+
+
+@pytest.mark.parametrize("dtype,ld", [(torch.bfloat16, 7), (torch.float32, 67),
+                                      (torch.float64, 5)])
+def test_gram_rejects_rows_that_are_not_16_byte_multiples(dtype, ld):
+    # rows of ld * sizeof bytes that are not whole 16-byte chunks are rejected before any launch
+    # (the tensor path moves whole tiles with bulk copies)
+    import ctypes
+    n, ka = 300, min(ld, 4)
+    T = torch.zeros((n, ld), dtype=dtype, device=DEV)
+    G = torch.full((2 * ka, 2 * ka), float("nan"), dtype=torch.float64, device=DEV)
+    scr = torch.empty(1 << 20, dtype=torch.uint8, device=DEV)
+    dt = {torch.bfloat16: sped.BF16, torch.float32: sped.F32, torch.float64: sped.F64}[dtype]
+    st = sped.lib().sped_gram(n, ctypes.c_void_p(T.data_ptr()), dt, ld, ka,
+                              ctypes.c_void_p(T.data_ptr()), dt, ld, ka,
+                              ctypes.c_void_p(G.data_ptr()), ctypes.c_void_p(scr.data_ptr()),
+                              scr.numel(), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    torch.cuda.synchronize()
+    assert st == sped.ERR_INVALID_ARG
+    assert b"multiple of 16" in sped.lib().sped_last_error()
+    assert torch.isnan(G).all()  # nothing launched

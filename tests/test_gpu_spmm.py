@@ -7,7 +7,7 @@ import torch
 import gen
 import oracle
 import paper_2207_14589_gb300 as sped
-from util_gpu import DEV, TOL, host, rel, stored, to_block
+from util_gpu import assert_close, DEV, TOL, host, rel, stored, to_block
 
 pytestmark = pytest.mark.gpu
 
@@ -42,7 +42,7 @@ def test_laplacian_step(gname, xt, yt, k, split):
     want = c * Xs + b * oracle.laplacian_apply(g, Xs)
     # the output storage decides the bound: inputs are compared as stored, F64 output means
     # F64 accumulation, otherwise F32 accumulation and rounding to the output type
-    assert rel(host(Y, k), want) <= TOL[yt]
+    assert_close(host(Y, k), want, TOL[yt])
     # padding columns were never written
     if Y.shape[1] > k:
         assert torch.isnan(Y[:, k:]).all()
@@ -59,7 +59,7 @@ def test_step_with_v_term(split):
     sped.poly_step(G, X, Y, k, alpha=0.7, beta=1.0, gamma=-0.2, V=V, split=split)
     torch.cuda.synchronize()
     want = 0.7 * V0 - 0.2 * X0 + oracle.laplacian_apply(g, X0)
-    assert rel(host(Y, k), want) <= 1e-12
+    assert_close(host(Y, k), want, 1e-12)
 
 
 def test_merge_equals_rowgroup_fp64():
@@ -72,7 +72,7 @@ def test_merge_equals_rowgroup_fp64():
     sped.poly_step(G, X, Y1, k, split=1)
     sped.poly_step(G, X, Y2, k, split=2)
     torch.cuda.synchronize()
-    assert rel(host(Y2, k), host(Y1, k)) <= 1e-14
+    assert_close(host(Y2, k), host(Y1, k), 1e-14)
 
 
 @pytest.mark.parametrize("ell", [1, 3, 9, 41])
@@ -91,7 +91,7 @@ def test_apply_poly_limit(ell, chain, yt, tol):
     sped.apply_poly(G, V, Y, k, chain_dtype=chain)
     torch.cuda.synchronize()
     want = oracle.poly_limit(g, stored(V0, vt), info.scale_s, ell)
-    assert rel(host(Y, k), want) <= tol
+    assert_close(host(Y, k), want, tol)
 
 
 @pytest.mark.parametrize("chain", [torch.float64, torch.bfloat16])
@@ -109,7 +109,7 @@ def test_apply_poly_two_step_chain(chain):
     sped.apply_poly(G, V, Y, k, chain_dtype=chain)
     torch.cuda.synchronize()
     want = oracle.poly_horner(g, stored(V0, vt), np.array(coeffs))
-    assert rel(host(Y, k), want) <= (1e-12 if chain == torch.float64 else 1e-2)
+    assert_close(host(Y, k), want, (1e-12 if chain == torch.float64 else 1e-2))
 
 
 def test_apply_poly_scale_rule_and_oddness():
@@ -135,17 +135,17 @@ def test_apply_poly_horner_taylor_exp_and_shift():
     G.set_polynomial(sped.POLY_TAYLOR_EXP, 12)
     sped.apply_poly(G, V, Y, k)
     torch.cuda.synchronize()
-    assert rel(host(Y, k), oracle.poly_horner(g, V0, oracle.taylor_exp_coeffs(12))) <= 1e-12
+    assert_close(host(Y, k), oracle.poly_horner(g, V0, oracle.taylor_exp_coeffs(12)), 1e-12)
     info = G.set_polynomial(sped.POLY_SHIFT, 1)
     sped.apply_poly(G, V, Y, k)
     torch.cuda.synchronize()
     want = info.lambda_star * V0 - oracle.laplacian_apply(g, V0)
-    assert rel(host(Y, k), want) <= 1e-12
+    assert_close(host(Y, k), want, 1e-12)
     coeffs = [0.5, -0.25, 0.125, 0.3]
     G.set_polynomial(sped.POLY_MONOMIAL, 3, coeffs=coeffs)
     sped.apply_poly(G, V, Y, k)
     torch.cuda.synchronize()
-    assert rel(host(Y, k), oracle.poly_horner(g, V0, np.array(coeffs))) <= 1e-12
+    assert_close(host(Y, k), oracle.poly_horner(g, V0, np.array(coeffs)), 1e-12)
 
 
 def test_apply_poly_taylor_log_small_radius():
@@ -162,7 +162,7 @@ def test_apply_poly_taylor_log_small_radius():
     torch.cuda.synchronize()
     c = -oracle.taylor_log_coeffs(60)
     c[0] += info.lambda_star
-    assert rel(host(Y, k), oracle.poly_horner(g, V0, c, shift=1e-3 - 1.0)) <= 1e-12
+    assert_close(host(Y, k), oracle.poly_horner(g, V0, c, shift=1e-3 - 1.0), 1e-12)
 
 
 def test_ones_fixed_by_limit_form():
@@ -219,7 +219,7 @@ def test_chebyshev_series_matches_oracle(ell, ct, tol, gname):
     torch.cuda.synchronize()
     Vs = stored(V0, V.dtype)
     want = oracle.poly_chebyshev(g, Vs, c, a, b)
-    assert rel(host(Y, k), want) <= tol
+    assert_close(host(Y, k), want, tol)
 
 
 def test_chebyshev_power_coefficients():

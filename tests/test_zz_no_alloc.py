@@ -1,9 +1,10 @@
 """sped_gram_noalloc: the Gram for callers that cannot allocate device memory (for example code
 in a host callback, a real-time loop or a plugin host, where cudaMalloc may synchronise the
 device or no allocator is available). It keeps its per-CTA partial sums in a static 4 MiB
-device array inside the library instead of caller scratch, and must give the same Gram as
-sped_gram. Checked through the C ABI on two calls in a row (the second call reuses the array
-the first one left behind). This file is named to run last."""
+device array inside the library instead of caller scratch. Checked through the C ABI on two
+calls in a row (the second call reuses the array the first one left behind) against the FP64
+product of the stored inputs, with torch's allocator counters and the device's free memory
+unchanged across the calls. This file is named to run last."""
 import ctypes
 
 import numpy as np
@@ -12,7 +13,7 @@ import torch
 
 import gen
 import paper_2207_14589_gb300 as sped
-from util_gpu import rel, to_block
+from util_gpu import assert_gram_close, stored, to_block
 
 pytestmark = pytest.mark.gpu
 
@@ -35,25 +36,43 @@ def _call(f, n, A, ka, B, kb, G):
              B.stride(0) if B is not None else 0, kb, ctypes.c_void_p(G.data_ptr()), stream)
 
 
-# tolerances as in test_gpu_solver.test_gram (relative Frobenius)
+def _torch_alloc_state():
+    st = torch.cuda.memory_stats()
+    return (torch.cuda.memory_allocated(), torch.cuda.memory_reserved(),
+            st.get("allocation.all.allocated", 0), st.get("segment.all.allocated", 0))
+
+
+# tolerances as in test_gpu_solver.test_gram, element-wise against the FP64 product
 @pytest.mark.parametrize("dtype,n,ka,kb,tol", [(torch.float32, 100003, 20, 20, 2e-6),
                                                (torch.float64, 50000, 32, 32, 1e-13),
                                                (torch.bfloat16, 7777, 7, 3, 1e-6),
                                                (torch.float32, 2500, 5, 0, 2e-6)])
-def test_gram_noalloc_matches_gram_twice(dtype, n, ka, kb, tol):
-    A = to_block(gen.gaussian_block(n, ka, seed=31), dtype)
-    B = to_block(gen.gaussian_block(n, kb, seed=32), dtype) if kb else None
-    want = sped.gram(A, ka, B, kb).cpu().numpy()
+def test_gram_noalloc_matches_fp64_product_twice(dtype, n, ka, kb, tol):
+    A0 = gen.gaussian_block(n, ka, seed=31)
+    B0 = gen.gaussian_block(n, kb, seed=32) if kb else None
+    A = to_block(A0, dtype)
+    B = to_block(B0, dtype) if kb else None
+    M = stored(A0, dtype) if not kb else np.concatenate([stored(A0, dtype), stored(B0, dtype)],
+                                                        axis=1)
+    want = M.T @ M
     f = _noalloc()
     K2 = ka + kb
-    for _ in range(2):
-        G = torch.full((K2, K2), float("nan"), dtype=torch.float64, device="cuda")
+    Gs = [torch.full((K2, K2), float("nan"), dtype=torch.float64, device="cuda")
+          for _ in range(2)]
+    torch.cuda.synchronize()
+    for t, G in enumerate(Gs):
+        before, free0 = _torch_alloc_state(), torch.cuda.mem_get_info()[0]
         st = _call(f, n, A, ka, B, kb, G)
         assert st == sped.OK, sped.lib().sped_last_error().decode()
         torch.cuda.synchronize()
-        got = G.cpu().numpy()
-        assert np.array_equal(got, got.T)
-        assert rel(got, want) <= tol
+        # nothing allocated: neither through torch's allocator nor on the device (the first
+        # call in a process may load the library's module holding the static array)
+        assert _torch_alloc_state() == before
+        if t == 1:
+            assert torch.cuda.mem_get_info()[0] == free0
+        assert_gram_close(G.cpu().numpy(), want, tol)
+    # the second call, which found the first call's partials in the array, gives the same bits
+    assert torch.equal(Gs[0], Gs[1])
 
 
 def test_gram_noalloc_rejects_more_than_64_columns():

@@ -29,3 +29,62 @@ def host(T, k):
 def rel(got, want):
     d = np.linalg.norm(want)
     return float(np.linalg.norm(got - want) / (d if d > 0 else 1.0))
+
+
+def errors(got, want):
+    """Relative errors of an n x k result (1-D: one column) against the oracle's, at four
+    granularities: the whole block (Frobenius), every column, every row and every entry. Each
+    is relative to the reference's own norm at that granularity, floored at the root mean
+    square of that granularity over the block (so that a row, column or entry that is small
+    because of cancellation is held to the accuracy of the block, not to its own size)."""
+    got = np.asarray(got, dtype=np.float64)
+    want = np.asarray(want, dtype=np.float64)
+    if want.ndim == 1:
+        got, want = got[:, None], want[:, None]
+    assert got.shape == want.shape, (got.shape, want.shape)
+    n, k = want.shape
+    err = got - want
+    fro = float(np.linalg.norm(want))
+    if fro == 0.0:
+        m = float(np.abs(err).max()) if err.size else 0.0
+        return {"fro": m, "col": m, "row": m, "entry": m}
+    col = np.linalg.norm(err, axis=0) / np.maximum(np.linalg.norm(want, axis=0), fro / np.sqrt(k))
+    row = np.linalg.norm(err, axis=1) / np.maximum(np.linalg.norm(want, axis=1), fro / np.sqrt(n))
+    ent = np.abs(err) / np.maximum(np.abs(want), fro / np.sqrt(n * k))
+    return {"fro": float(np.linalg.norm(err)) / fro, "col": float(col.max()),
+            "row": float(row.max()), "entry": float(ent.max())}
+
+
+# per-granularity factors on a block tolerance: a row of k entries or a column of n entries
+# spreads its rounding errors less evenly than the whole block, and a single entry least
+FACTORS = {"fro": 1.0, "col": 2.0, "row": 2.0, "entry": 4.0}
+
+
+def assert_close(got, want, tol):
+    """Element-wise parity: the block within tol (relative Frobenius, the tolerance of the
+    method's stated bound), every column and every row within 2 tol, every entry within 4 tol
+    (see errors()). A wrong column, a few wrong rows or a single wrong entry of a large block
+    fail here even when the block's Frobenius error stays small."""
+    got = np.asarray(got, dtype=np.float64)
+    assert np.isfinite(got).all(), "non-finite values in the result"
+    e = errors(got, want)
+    bad = {g: v for g, v in e.items() if not v <= FACTORS[g] * tol}
+    assert not bad, f"tolerance {tol:g} exceeded: {bad} (all: {e})"
+    return e
+
+
+def assert_gram_close(got, want, tol):
+    """Element-wise parity of a Gram matrix: |G_ij - W_ij| <= tol sqrt(W_ii W_jj) for every
+    (i, j) (the Cauchy-Schwarz scale of the entry), exact symmetry, and the relative Frobenius
+    error within tol."""
+    got = np.asarray(got, dtype=np.float64)
+    want = np.asarray(want, dtype=np.float64)
+    assert np.isfinite(got).all()
+    assert np.array_equal(got, got.T)
+    d = np.sqrt(np.maximum(np.diag(want), 0.0))
+    scale = np.outer(d, d)
+    scale[scale == 0.0] = 1.0
+    e = float((np.abs(got - want) / scale).max())
+    assert e <= tol, f"entry-wise Gram error {e:.3e} > {tol:g}"
+    assert rel(got, want) <= tol
+    return e
