@@ -682,32 +682,26 @@ def with_edge_weights(g, w_edge):
 # ----------------------------------------------------------------------------------------
 # Sections 1 and 2.1: hard clustering by k-means on the rows of the eigenvector block
 # ----------------------------------------------------------------------------------------
-def kmeans(X, n_clusters, seed, max_iter=100):
-    """k-means++ seeding then Lloyd iterations until the labels stop changing.
+def _sqdist(P, C):
+    """Squared distances sum_d (p_d - c_d)^2, accumulated in dimension order."""
+    out = np.zeros((P.shape[0], C.shape[0]))
+    for t in range(P.shape[1]):
+        out += (P[:, t][:, None] - C[None, :, t]) ** 2
+    return out
 
-    The paper only says k-means on the embedding (Section 1, Section 2.1). Readings:
-    seeding draws from Philox4x32-10 with key (seed) and counter (c, 0, 0, 0x6B6D) for the
-    c-th centre: centre 0 is a bounded draw in [0, n); centre c >= 1 takes the first row
-    whose running sum of squared distances exceeds u * total, u = (word + 0.5) 2^-32.
-    Distances are sum_d (x_d - m_d)^2 in dimension order; ties go to the lowest centroid;
-    an empty cluster is re-seeded with the point farthest from its centroid (lowest index);
-    labels are renumbered by first occurrence in row order. Parity unpinned beyond the
-    separated-cluster and brute-force pins."""
+
+def kmeanspp_seeds(X, n_clusters, seed):
+    """k-means++ seeding (Arthur and Vassilvitskii, 2007): the first centre uniform over the
+    rows, every further centre drawn with probability proportional to the squared distance
+    D^2(x) to the nearest centre chosen so far. Draws from Philox4x32-10 with key (seed) and
+    counter (c, 0, 0, 0x6B6D) for the c-th centre: centre 0 is a bounded draw in [0, n);
+    centre c >= 1 is the first row whose running sum of D^2 exceeds u * total,
+    u = (word + 0.5) 2^-32. Returns the row indices of the centres."""
     X = np.asarray(X, dtype=np.float64)
-    n, d = X.shape
-    K = n_clusters
-
-    def sqdist(P, C):
-        out = np.zeros((P.shape[0], C.shape[0]))
-        for t in range(d):
-            out += (P[:, t][:, None] - C[None, :, t]) ** 2
-        return out
-
-    centers = np.empty((K, d))
-    first = int(bounded_draws(seed, 0, 0, 0x6B6D, n, 1)[0])
-    centers[0] = X[first]
-    D2 = sqdist(X, centers[:1])[:, 0]
-    for c in range(1, K):
+    n = X.shape[0]
+    picks = [int(bounded_draws(seed, 0, 0, 0x6B6D, n, 1)[0])]
+    D2 = _sqdist(X, X[picks[0]][None, :])[:, 0]
+    for c in range(1, n_clusters):
         word = philox4x32_10([c, 0, 0, 0x6B6D], [seed & 0xFFFFFFFF, seed >> 32])[0]
         u = (word + 0.5) * 2.0 ** -32
         cum = 0.0
@@ -719,8 +713,25 @@ def kmeans(X, n_clusters, seed, max_iter=100):
             if cum > target:
                 pick = i
                 break
-        centers[c] = X[pick]
-        D2 = np.minimum(D2, sqdist(X, centers[c:c + 1])[:, 0])
+        picks.append(pick)
+        D2 = np.minimum(D2, _sqdist(X, X[pick][None, :])[:, 0])
+    return picks
+
+
+def kmeans(X, n_clusters, seed, max_iter=100):
+    """k-means++ seeding (kmeanspp_seeds) then Lloyd iterations until the labels stop changing.
+
+    The paper only says k-means on the embedding (Section 1, Section 2.1). Readings:
+    distances are sum_d (x_d - m_d)^2 in dimension order; ties go to the lowest centroid;
+    an empty cluster is re-seeded with the point farthest from its centroid (lowest index);
+    labels are renumbered by first occurrence in row order. Pinned by separated clusters
+    (exact labels), brute force over all partitions of tiny sets, and the seeding's
+    distribution and forced choices (tests/test_oracle_solver.py)."""
+    X = np.asarray(X, dtype=np.float64)
+    n, d = X.shape
+    K = n_clusters
+    sqdist = _sqdist
+    centers = X[kmeanspp_seeds(X, K, seed)].copy()
     labels = None
     for _ in range(max_iter):
         dist = sqdist(X, centers)

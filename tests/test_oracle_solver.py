@@ -106,6 +106,41 @@ def test_kmeans_brute_force_tiny():
     assert sse == pytest.approx(best[0], rel=1e-12)
 
 
+def test_kmeanspp_seeding_distribution():
+    # k-means++ (Arthur and Vassilvitskii, 2007): the first centre is uniform over the rows and
+    # the second is drawn with probability D^2(x) / sum D^2 given the first
+    X = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 2.0], [3.0, 1.0], [-1.0, -1.0], [2.0, 2.0]])
+    n, trials = len(X), 6000
+    first = np.zeros(n)
+    pair = np.zeros((n, n))
+    for s in range(trials):
+        p = oracle.kmeanspp_seeds(X, 2, seed=s)
+        first[p[0]] += 1
+        pair[p[0], p[1]] += 1
+    chi2 = float(np.sum((first - trials / n) ** 2 / (trials / n)))
+    assert chi2 < 5 + 6 * np.sqrt(10)  # 5 dof
+    D2 = np.sum((X[:, None, :] - X[None, :, :]) ** 2, axis=2)
+    for f0 in range(n):
+        m = pair[f0].sum()
+        want = m * D2[f0] / D2[f0].sum()
+        assert pair[f0, f0] == 0  # the first centre has D^2 = 0
+        ok = want > 0
+        chi2 = float(np.sum((pair[f0, ok] - want[ok]) ** 2 / want[ok]))
+        assert chi2 < 4 + 6 * np.sqrt(8), (f0, pair[f0], want)
+
+
+def test_kmeanspp_forced_choices():
+    # rows at the first centre have D^2 = 0 and are never drawn again: with only one row away
+    # from it, the second centre is that row whatever the draw; then a third centre can only
+    # be the remaining distinct row
+    X = np.array([[1.0, 1.0]] * 5 + [[4.0, 5.0]] + [[1.0, 1.0]] * 3 + [[-2.0, 0.5]])
+    for s in range(50):
+        p = oracle.kmeanspp_seeds(X, 3, seed=s)
+        if p[0] not in (5, 9):
+            assert {p[1], p[2]} == {5, 9}
+        assert len({tuple(X[i]) for i in p}) == 3
+
+
 def _fd_grad_V(f, V, h=1e-4):
     G = np.empty_like(V)
     for idx in np.ndindex(V.shape):

@@ -88,3 +88,27 @@ def assert_gram_close(got, want, tol):
     assert e <= tol, f"entry-wise Gram error {e:.3e} > {tol:g}"
     assert rel(got, want) <= tol
     return e
+
+
+def assert_step_close(got, want, step, Y, tol, seed=0, directions=3):
+    """Element-wise parity of a solver step's output whose input Y = p(L) V carries the chain's
+    storage bound tol (relative Frobenius). The step maps Y to its output through the eta Y
+    term and the Gram-derived coefficients, which can amplify an error in Y, unevenly across
+    columns when a column nearly cancels before its normalisation. The gain is measured on the
+    oracle: Y is perturbed by a relative tol in a few seeded Gaussian directions, and the
+    largest errors of the perturbed steps against `want` at every granularity (errors()) set
+    the bound, times 3 (a storage error can line up with the step's amplifying directions
+    better than a random direction does) and 1.5 of margin; never below FACTORS * tol."""
+    ep = {}
+    for d in range(directions):
+        D = np.random.default_rng(seed * 7919 + d).standard_normal(Y.shape)
+        Yp = Y + tol * np.linalg.norm(Y) * D / np.linalg.norm(D)
+        for g, v in errors(step(Yp), want).items():
+            ep[g] = max(ep.get(g, 0.0), v)
+    got = np.asarray(got, dtype=np.float64)
+    assert np.isfinite(got).all(), "non-finite values in the result"
+    e = errors(got, want)
+    bound = {g: 1.5 * max(FACTORS[g] * tol, 3.0 * ep[g]) for g in e}
+    bad = {g: (e[g], bound[g]) for g in e if not e[g] <= bound[g]}
+    assert not bad, f"step errors above the propagated bound: {bad} (all: {e})"
+    return e
