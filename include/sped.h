@@ -279,6 +279,21 @@ sped_status sped_gram(int64_t n, const void *d_A, sped_dtype a_t, int lda, int k
 
 sped_status sped_gram_scratch_size(int64_t n, int ka, int kb, size_t *bytes);
 
+/* Device-detected errors that have no synchronising call of their own. Synchronises `stream`,
+ * then reads and clears this library's device status word on the current device: returns
+ * SPED_ERR_TIMEOUT when a bounded device-side wait gave up since the last read (the tensor-core
+ * Gram's waits on its bulk copies and MMAs; the Gram of that call is NaN), else SPED_OK.
+ * sped_solve_bottom_k reads the word too and returns SPED_ERR_TIMEOUT in the same case. The
+ * word is shared by every stream and host thread using the device. */
+sped_status sped_device_status(void *stream);
+
+/* Test control of the tensor-core Gram's bounded waits, for the calling process: wait_limit is
+ * the number of polls after which a wait gives up (0 = the default of 2^22 polls); skip_fills
+ * != 0 makes the kernel issue no bulk copies (and so no MMAs), so its first wait runs out with
+ * nothing in flight: the CTA frees its tensor memory, writes NaN partials and sets the status
+ * word read by sped_device_status. For tests of the timeout path only; leave at (0, 0). */
+sped_status sped_test_gram_waits(uint32_t wait_limit, int skip_fills);
+
 /* sped_gram for callers that cannot allocate device memory: for example code running inside a
  * host callback, a real-time loop or a plugin host, where cudaMalloc (which may synchronise the
  * device) is not allowed and no device allocator is handed in. The paper has no counterpart;

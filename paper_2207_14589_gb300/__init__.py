@@ -127,6 +127,8 @@ def lib():
         "sped_poly_moments": [vp, vp, i32, i32, i32, i32, i32, dbl, dbl, vp, vp, sz, vp],
         "sped_poly_moments_scratch_size": [vp, i32, i32, P(sz)],
         "sped_probe_gather": [vp, i32, vp, i32, vp, i32, i32, u64, vp],
+        "sped_device_status": [vp],
+        "sped_test_gram_waits": [ctypes.c_uint32, i32],
         "sped_sample_edges": [vp, u64, ctypes.c_uint32, i64, i32, vp, vp, vp, vp, vp],
         "sped_edge_step": [i64, i32, vp, vp, vp, i64, dbl, vp, i32, i32, vp, i32, i32, vp, i32,
                            i32, dbl, dbl, dbl, vp, vp],
@@ -421,6 +423,17 @@ def gram(A, ka, B=None, kb=0, G=None, scratch=None, stream=None):
     _check(lib().sped_gram(n, _ptr(A), at, lda, ka, _ptr(B), bt, ldb, kb, _ptr(G),
                            _ptr(scratch), scratch.numel(), _stream(stream)))
     return G
+
+
+def device_status(stream=None):
+    """Synchronise the stream and raise SpedError(ERR_TIMEOUT) if a bounded device-side wait gave
+    up since the last check (sped_device_status); the status word is cleared."""
+    _check(lib().sped_device_status(_stream(stream)))
+
+
+def test_gram_waits(wait_limit=0, skip_fills=False):
+    """Test control of the tensor-core Gram's bounded waits (sped_test_gram_waits)."""
+    _check(lib().sped_test_gram_waits(int(wait_limit), int(bool(skip_fills))))
 
 
 def step_opts(solver=MU_EG, eta=1.0, chain_dtype=torch.float32, y_dtype=torch.float32,

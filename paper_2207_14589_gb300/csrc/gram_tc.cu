@@ -27,8 +27,10 @@
 // and the next 8-row group 256 bytes away (stride byte offset).
 //
 // Every wait is bounded: if a completion is not observed within the limit the CTA stops issuing
-// work, waits (bounded) for the copies and MMAs it issued, releases its tensor memory and
-// writes NaN partials, so the caller sees a non-finite Gram instead of a hang.
+// work, waits (bounded) for the copies and MMAs it issued, releases its tensor memory, writes
+// NaN partials and sets bit 0 of the library's device status word, so the caller sees a
+// non-finite Gram and SPED_ERR_TIMEOUT from sped_device_status instead of a hang.
+#include <atomic>
 #include <cmath>
 
 #include "sped_internal.cuh"
@@ -111,9 +113,13 @@ __device__ __forceinline__ bool mbar_test(uint32_t mbar, uint32_t parity) {
     return ok != 0;
 }
 
-// bounded wait for the given phase parity; false on timeout
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-    for (uint32_t it = 0; it < TC_WAIT_LIMIT; ++it) {
+// Device status word of this library on the current device: bit 0 is set when a bounded wait of
+// the tensor Gram gave up. sped_device_status reads and clears it.
+static __device__ unsigned int g_device_status;
+
+// bounded wait for the given phase parity (at most `limit` polls); false on timeout
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, uint32_t limit) {
+    for (uint32_t it = 0; it < limit; ++it) {
         if (mbar_test(mbar, parity)) return true;
         if (it > 64) __nanosleep(64);
     }
@@ -174,7 +180,7 @@ __device__ __forceinline__ void two_sum(float &s, float &e, float x) {
 template <typename Ta, typename Tb, int S>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_gram_tc(int64_t n, const Ta *__restrict__ A, int lda, int ka, const Tb *__restrict__ B, int ldb,
-          int kb, double *__restrict__ partial) {
+          int kb, double *__restrict__ partial, uint32_t wait_limit, int skip_fills) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     TcSmem &sm = *reinterpret_cast<TcSmem *>(
         smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023));
@@ -228,9 +234,10 @@ k_gram_tc(int64_t n, const Ta *__restrict__ A, int lda, int ka, const Tb *__rest
     auto issue = [&]() {  // next fill, once its stage has been released by every warp
         const int64_t f = issued;
         if (f >= my_tiles) return true;
+        if (skip_fills) return true;  // test of the timeout path: nothing is ever in flight
         const int rs = (int)(f % TC_NRAW);
         if (f >= TC_NRAW &&
-            !mbar_wait(smem_u32(&sm.empty_bar[rs]), (uint32_t)(((f / TC_NRAW) - 1) & 1)))
+            !mbar_wait(smem_u32(&sm.empty_bar[rs]), (uint32_t)(((f / TC_NRAW) - 1) & 1), wait_limit))
             return false;
         const int64_t r0 = (blockIdx.x + f * gridDim.x) * (int64_t)TC_TILE;
         const int rows = (int)(n - r0 < TC_TILE ? n - r0 : TC_TILE);
@@ -260,9 +267,9 @@ k_gram_tc(int64_t n, const Ta *__restrict__ A, int lda, int ka, const Tb *__rest
         if (t == 0) {
             bool good = sm.timed_out == 0;
             if (good && issued < my_tiles && !issue()) good = false;
-            if (good && !mbar_wait(smem_u32(&sm.full_bar[rs]), (uint32_t)((it / TC_NRAW) & 1)))
+            if (good && !mbar_wait(smem_u32(&sm.full_bar[rs]), (uint32_t)((it / TC_NRAW) & 1), wait_limit))
                 good = false;
-            if (good && pending[st] && !mbar_wait(smem_u32(&sm.mma_bar[st]), mma_par[st]))
+            if (good && pending[st] && !mbar_wait(smem_u32(&sm.mma_bar[st]), mma_par[st], wait_limit))
                 good = false;
             if (!good) sm.timed_out = 1;
             sm.wait_ok = good ? 1 : 0;
@@ -336,7 +343,7 @@ k_gram_tc(int64_t n, const Ta *__restrict__ A, int lda, int ka, const Tb *__rest
         if ((it + 1) % TC_FLUSH == 0 || it + 1 == my_tiles) {
             // ---- fold the accumulator into the double-float running sums in tensor memory
             if (t == 0) {
-                const bool good = mbar_wait(smem_u32(&sm.mma_bar[st]), mma_par[st]);
+                const bool good = mbar_wait(smem_u32(&sm.mma_bar[st]), mma_par[st], wait_limit);
                 if (!good) sm.timed_out = 1;
                 sm.wait_ok = good ? 1 : 0;
             }
@@ -374,11 +381,12 @@ k_gram_tc(int64_t n, const Ta *__restrict__ A, int lda, int ka, const Tb *__rest
     if (t == 0) {
         if (!ok) sm.timed_out = 1;
         for (int s = 0; s < 2; ++s)
-            if (pending[s] && !mbar_wait(smem_u32(&sm.mma_bar[s]), mma_par[s])) sm.timed_out = 2;
+            if (pending[s] && !mbar_wait(smem_u32(&sm.mma_bar[s]), mma_par[s], wait_limit)) sm.timed_out = 2;
         // fills issued but not consumed by the loop (only after a timeout)
         if (!ok)
             for (int64_t f = 0; f < issued; ++f)
-                if (!mbar_wait(smem_u32(&sm.full_bar[f % TC_NRAW]), (uint32_t)((f / TC_NRAW) & 1)))
+                if (!mbar_wait(smem_u32(&sm.full_bar[f % TC_NRAW]), (uint32_t)((f / TC_NRAW) & 1),
+                               wait_limit))
                     sm.timed_out = 2;
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -388,6 +396,7 @@ k_gram_tc(int64_t n, const Ta *__restrict__ A, int lda, int ka, const Tb *__rest
     float *fin_hi = reinterpret_cast<float *>(&sm.stage[0][0]);
     float *fin_lo = fin_hi + 128 * 128;
     const int bad = sm.timed_out;
+    if (bad && t == 0) atomicOr(&g_device_status, 1u);
     if (bad != 2 && folder) {
 #pragma unroll 1
         for (int h = 0; h < 32; h += 16) {
@@ -481,14 +490,21 @@ size_t gram_tc_scratch(int64_t n, int ka, int kb) {
     return sizeof(double) * (size_t)K2 * K2 * 512;
 }
 
+// test controls of the bounded waits (sped_test_gram_waits): poll limit (0 = TC_WAIT_LIMIT) and
+// whether the kernel skips issuing its bulk copies
+static std::atomic<uint32_t> g_tc_wait_limit{0};
+static std::atomic<int> g_tc_skip_fills{0};
+
 template <typename Ta, typename Tb, int S>
 static sped_status run_tc(int64_t n, const void *A, int lda, int ka, const void *B, int ldb, int kb,
                           double *G, double *partial, int ctas, cudaStream_t st) {
     const size_t smem = sizeof(TcSmem) + 1024;
     auto kern = k_gram_tc<Ta, Tb, S>;
     SPED_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const uint32_t lim = g_tc_wait_limit.load();
     kern<<<ctas, TC_THREADS, smem, st>>>(n, (const Ta *)A, lda, ka, (const Tb *)B, ldb, kb,
-                                         partial);
+                                         partial, lim ? lim : TC_WAIT_LIMIT,
+                                         g_tc_skip_fills.load());
     SPED_CHECK_LAUNCH("k_gram_tc");
     const int K2 = ka + kb;
     k_gram_tc_reduce<<<(K2 * K2 + RED_OUT - 1) / RED_OUT, RED_OUT * RED_GROUPS, 0, st>>>(
@@ -523,3 +539,26 @@ sped_status launch_gram_tc(int64_t n, const void *A, sped_dtype at, int lda, int
 }
 
 }  // namespace sped
+
+using namespace sped;
+
+extern "C" {
+
+sped_status sped_device_status(void *stream) {
+    SPED_CUDA(cudaStreamSynchronize(as_stream(stream)));
+    unsigned int v = 0, zero = 0;
+    SPED_CUDA(cudaMemcpyFromSymbol(&v, g_device_status, sizeof(v)));
+    if (v) SPED_CUDA(cudaMemcpyToSymbol(g_device_status, &zero, sizeof(zero)));
+    if (v & 1u)
+        return fail(SPED_ERR_TIMEOUT, "a bounded wait of the tensor-core Gram gave up (its Gram "
+                                      "is NaN)");
+    return SPED_OK;
+}
+
+sped_status sped_test_gram_waits(uint32_t wait_limit, int skip_fills) {
+    g_tc_wait_limit.store(wait_limit);
+    g_tc_skip_fills.store(skip_fills ? 1 : 0);
+    return SPED_OK;
+}
+
+}  // extern "C"

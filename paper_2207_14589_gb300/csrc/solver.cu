@@ -639,6 +639,8 @@ sped_status sped_solve_bottom_k(const sped_graph *g, const sped_solve_opts *opts
             SPED_CUDA(cudaMemcpyAsync(&h_err, base + coef_off + offsetof(Coefs, err), sizeof(int),
                                       cudaMemcpyDeviceToHost, st));
             SPED_CUDA(cudaStreamSynchronize(st));
+            // a bounded wait that gave up leaves a NaN Gram: report the cause, not the symptom
+            if (h_err) SPED_TRY(sped_device_status(stream));
             if (h_err & SOLVE_ERR_NOT_PD)
                 return fail(SPED_ERR_NUMERIC, "solve: Gram of V + eta Y not positive definite");
             if (h_err & SOLVE_ERR_NAN) return fail(SPED_ERR_NUMERIC, "solve: non-finite norm");
@@ -665,6 +667,7 @@ sped_status sped_solve_bottom_k(const sped_graph *g, const sped_solve_opts *opts
     }
     SPED_CUDA(cudaStreamSynchronize(st));
     if (report) *report = rep;
+    SPED_TRY(sped_device_status(stream));
     if (!rep.converged)
         return fail(SPED_ERR_NOT_CONVERGED, "solve_bottom_k: %d steps, residual %.3e > tol %.3e",
                     rep.steps, rep.final_residual, opts->tol);

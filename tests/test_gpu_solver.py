@@ -7,7 +7,7 @@ import torch
 import gen
 import oracle
 import paper_2207_14589_gb300 as sped
-from util_gpu import DEV, assert_close, assert_gram_close, host, rel, stored, to_block
+from util_gpu import DEV, assert_close, assert_gram_close, assert_step_close, host, stored, to_block
 
 pytestmark = pytest.mark.gpu
 
@@ -79,8 +79,9 @@ def test_eig_step_mixed_precision_close_to_fp64():
     sped.eig_step(G, V, k, opts)
     torch.cuda.synchronize()
     Vs = stored(V0, torch.float32)
-    want = oracle.mu_eg_step(Vs, oracle.poly_limit(g, Vs, info.scale_s, 21), 1.0)
-    assert_close(host(V, k), want, 1e-2)
+    Y = oracle.poly_limit(g, Vs, info.scale_s, 21)
+    want = oracle.mu_eg_step(Vs, Y, 1.0)
+    assert_step_close(host(V, k), want, lambda Yp: oracle.mu_eg_step(Vs, Yp, 1.0), Y, 1e-2)
 
 
 def _sbm_n2000_k4():
@@ -111,8 +112,9 @@ def test_bf16_shadow_tracks_master_and_feeds_the_chain():
     sped.eig_step(G, V, k, opts)
     torch.cuda.synchronize()
     assert torch.equal(Vb[:, :k], V[:, :k].to(torch.bfloat16))
-    want = oracle.mu_eg_step(V1, oracle.poly_limit(g, V1, info.scale_s, ell), 1.0)
-    assert_close(host(V, k), want, 1e-2)
+    Y1 = oracle.poly_limit(g, V1, info.scale_s, ell)
+    want = oracle.mu_eg_step(V1, Y1, 1.0)
+    assert_step_close(host(V, k), want, lambda Yp: oracle.mu_eg_step(V1, Yp, 1.0), Y1, 1e-2)
     # the shadow needs an F32 master
     V64 = to_block(V0, torch.float64)
     with pytest.raises(sped.SpedError):
@@ -265,3 +267,46 @@ def test_gram_rejects_rows_that_are_not_16_byte_multiples(dtype, ld):
     assert st == sped.ERR_INVALID_ARG
     assert b"multiple of 16" in sped.lib().sped_last_error()
     assert torch.isnan(G).all()  # nothing launched
+
+
+def test_gram_wait_timeout_surfaces_as_status():
+    # the tensor Gram's bounded waits: with its bulk copies skipped (nothing in flight) and a
+    # short poll limit, the first wait runs out; the CTAs free their tensor memory and return,
+    # the Gram is NaN and the next status read reports SPED_ERR_TIMEOUT. The context stays
+    # usable: the same call afterwards is exact again and the status is clear.
+    n, k = 5000, 20
+    A0 = gen.gaussian_block(n, k, seed=61)
+    A = to_block(A0, torch.float32)
+    want = stored(A0, torch.float32).T @ stored(A0, torch.float32)
+    sped.device_status()  # start from a clear word
+    try:
+        sped.test_gram_waits(wait_limit=2000, skip_fills=True)
+        G = sped.gram(A, k)
+        with pytest.raises(sped.SpedError) as e:
+            sped.device_status()
+        assert e.value.status == sped.ERR_TIMEOUT
+        assert torch.isnan(G).all()
+    finally:
+        sped.test_gram_waits(0, False)
+    sped.device_status()  # cleared by the read above
+    G = sped.gram(A, k)
+    sped.device_status()
+    assert_gram_close(G.cpu().numpy(), want, 2e-6)
+
+
+def test_solve_reports_a_timed_out_wait():
+    g = gen.sbm(3000, 3, 0.02, 0.001, seed=62)
+    G = sped.Graph.from_csr(g)
+    G.set_polynomial(sped.POLY_LIMIT_EXP, 9)
+    k = 4
+    V = to_block(gen.gaussian_block(g.n, k, seed=63), torch.float32)
+    opts = sped.solve_opts(sped.OJA, 0.0, torch.bfloat16, torch.float32, max_steps=3,
+                           check_every=1)
+    try:
+        sped.test_gram_waits(wait_limit=2000, skip_fills=True)
+        with pytest.raises(sped.SpedError) as e:
+            sped.solve_bottom_k(G, V, k, opts)
+        assert e.value.status == sped.ERR_TIMEOUT
+    finally:
+        sped.test_gram_waits(0, False)
+    sped.device_status()
