@@ -965,7 +965,7 @@ def measure_power_law(sped, torch, dev, stream, n=16_000_000, k=32, ell=251, tar
     251 with s = 2 / lambda_bound. Times one merge-path step, one row-group step on the same
     graph, and the whole p(L) V."""
     t0 = time.perf_counter()
-    g = gen.chung_lu_clusters(n, target_nnz=target_nnz, seed=SEED)
+    g = gen.chung_lu_clusters(n, target_nnz=target_nnz or None, seed=SEED, device=dev)
     gen_s = time.perf_counter() - t0
     G = sped.Graph.from_csr(g, device=dev)
     info = G.set_polynomial(sped.POLY_LIMIT_EXP, ell)
@@ -1099,8 +1099,9 @@ def run_ours(args, rank, world, local_rank):
     Yg = sped.alloc_block(g.n, k, torch.bfloat16, dev)
     gather = {"chain_step_us": launch_ms * 1e3, "gathers_per_launch": g.nnz,
               "bytes_per_gather": sped.padded_ld(k, torch.bfloat16) * 2}
-    for mode, name in ((0, "csr_order"), (1, "hashed_rows"), (2, "consecutive_rows")):
-        probe = lambda: sped.probe_gather(G, Xg, Yg, k, mode=mode, seed=SEED)
+    from paper_2207_14589_gb300 import probe as gprobe
+    for name, mode in gprobe.MODES.items():
+        probe = lambda: gprobe.probe_gather(G.row_ptr, G.col_idx, Xg, Yg, k, mode=mode, seed=SEED)
         probe()
         us = _timed(torch, stream, probe, 20) * 1e3
         gather[f"{name}_us"] = us
@@ -1206,7 +1207,7 @@ def run_ours(args, rank, world, local_rank):
         for name, fn in runs.items():
             if want is None or name in want:
                 extra[name] = fn()
-    if rank == 0 and args.power_law:
+    if rank == 0 and not args.no_power_law:
         extra["power_law"] = measure_power_law(sped, torch, dev, stream, n=args.power_law_n,
                                                target_nnz=args.target_nnz)
     if rank == 0 and not args.no_ttk:
@@ -1346,13 +1347,13 @@ def main():
                          "three_room, fitted_poly); default all")
     ap.add_argument("--batched-graphs", type=int, default=4096,
                     help="number of graphs of the batched measurement")
-    ap.add_argument("--power-law", action="store_true",
-                    help="also time the merge-path chain on the 16M-node Chung-Lu graph "
-                         "(about 2 minutes of host-side graph generation)")
+    ap.add_argument("--no-power-law", action="store_true",
+                    help="skip the merge-path chain on the 16M-node Chung-Lu graph")
     ap.add_argument("--power-law-n", type=int, default=16_000_000,
                     help="nodes of the Chung-Lu graph for --power-law")
-    ap.add_argument("--target-nnz", type=float, default=None,
-                    help="scale the Chung-Lu expected degrees to this many stored entries")
+    ap.add_argument("--target-nnz", type=float, default=3.2e8,
+                    help="scale the Chung-Lu expected degrees to this many stored entries "
+                         "(0: the degree law's own, about 1.9e8)")
     ap.add_argument("--extras-out", default=None,
                     help="also write every measurement (headline and extras) to this JSON file")
     ap.add_argument("--spectrum", action="store_true",

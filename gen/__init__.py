@@ -56,11 +56,40 @@ class CSRGraph:
         return int(self.degrees().max()) if self.n else 0
 
 
-def from_edges(n: int, a, b, w=None, labels=None, name: str = "") -> CSRGraph:
+def _stable_argsort(keys, device=None):
+    """Indices that sort int64 keys, equal keys in input order (numpy, or torch on `device`:
+    the same permutation, for large generators)."""
+    if device is None:
+        return np.argsort(keys, kind="stable")
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(keys)).to(device)
+    return torch.sort(t, stable=True).indices.cpu().numpy()
+
+
+def _first_of_each(keys, device=None):
+    """Ascending indices of the first occurrence of every distinct key."""
+    order = _stable_argsort(keys, device)
+    ks = keys[order]
+    head = np.ones(len(ks), dtype=bool)
+    head[1:] = ks[1:] != ks[:-1]
+    return np.sort(order[head])
+
+
+def _searchsorted_right(cum, r, device=None):
+    if device is None:
+        return np.searchsorted(cum, r, side="right")
+    import torch
+    c = torch.from_numpy(np.ascontiguousarray(cum)).to(device)
+    q = torch.from_numpy(np.ascontiguousarray(r)).to(device)
+    return torch.searchsorted(c, q, right=True).cpu().numpy()
+
+
+def from_edges(n: int, a, b, w=None, labels=None, name: str = "", device=None) -> CSRGraph:
     """Build a symmetric CSR from undirected edge endpoint arrays.
 
     Self-loops are dropped; duplicates of an undirected edge are merged, keeping the first
-    weight in input order (the input-hygiene reading for unspecified inputs).
+    weight in input order (the input-hygiene reading for unspecified inputs). `device` (a torch
+    device) runs the two sorts there; the result is the same.
     """
     a = np.asarray(a, dtype=np.int64).ravel()
     b = np.asarray(b, dtype=np.int64).ravel()
@@ -71,14 +100,13 @@ def from_edges(n: int, a, b, w=None, labels=None, name: str = "") -> CSRGraph:
     lo = np.minimum(a, b)
     hi = np.maximum(a, b)
     key = lo * np.int64(n) + hi
-    _, first = np.unique(key, return_index=True)
-    first.sort()
+    first = _first_of_each(key, device)
     lo, hi = lo[first], hi[first]
     if w is not None:
         w = w[first]
     rows = np.concatenate([lo, hi])
     cols = np.concatenate([hi, lo])
-    order = np.argsort(rows * np.int64(n) + cols, kind="stable")
+    order = _stable_argsort(rows * np.int64(n) + cols, device)
     rows, cols = rows[order], cols[order]
     counts = np.bincount(rows, minlength=n)
     row_ptr = np.zeros(n + 1, dtype=np.int64)
@@ -296,10 +324,11 @@ def random_graph(n: int, m: int, seed: int = DEFAULT_SEED, hub: int | None = Non
 def chung_lu_clusters(n: int, n_clusters: int = 64, gamma: float = 2.5, d_min: float = 4.0,
                       d_max: float = 1e4, sigma: float = 1.0, intra_frac: float = 0.9,
                       target_nnz: float | None = None, weighted: bool = True,
-                      seed: int = DEFAULT_SEED) -> CSRGraph:
+                      seed: int = DEFAULT_SEED, device=None) -> CSRGraph:
     """Planted-cluster Chung-Lu graph: expected degrees from a power law with exponent
     ``gamma`` on [d_min, d_max], clusters of log-normal sizes, a fraction ``intra_frac`` of
-    edge ends inside the cluster. Nodes are ordered by cluster. Weights U(0.5, 1.5)."""
+    edge ends inside the cluster. Nodes are ordered by cluster. Weights U(0.5, 1.5).
+    `device` (a torch device) runs the searches and sorts there; the graph is the same."""
     rng = np.random.default_rng(seed)
     e = 1.0 - gamma
     u = rng.random(n)
@@ -326,21 +355,21 @@ def chung_lu_clusters(n: int, n_clusters: int = 64, gamma: float = 2.5, d_min: f
         lo = cum[off[c] - 1] if off[c] > 0 else 0.0
         r1 = lo + rng.random(m_c[c]) * s_c[c]
         r2 = lo + rng.random(m_c[c]) * s_c[c]
-        a_list.append(np.minimum(np.searchsorted(cum, r1, side="right"), off[c + 1] - 1))
-        b_list.append(np.minimum(np.searchsorted(cum, r2, side="right"), off[c + 1] - 1))
+        a_list.append(np.minimum(_searchsorted_right(cum, r1, device), off[c + 1] - 1))
+        b_list.append(np.minimum(_searchsorted_right(cum, r2, device), off[c + 1] - 1))
     m_out = int(rng.poisson((1.0 - intra_frac) * total / 2.0))
     if m_out:
         r1 = rng.random(m_out) * total
         r2 = rng.random(m_out) * total
-        ua = np.minimum(np.searchsorted(cum, r1, side="right"), n - 1)
-        va = np.minimum(np.searchsorted(cum, r2, side="right"), n - 1)
+        ua = np.minimum(_searchsorted_right(cum, r1, device), n - 1)
+        va = np.minimum(_searchsorted_right(cum, r2, device), n - 1)
         keep = labels[ua] != labels[va]
         a_list.append(ua[keep])
         b_list.append(va[keep])
     a = np.concatenate(a_list)
     b = np.concatenate(b_list)
     w = rng.uniform(0.5, 1.5, size=len(a)).astype(np.float32) if weighted else None
-    return from_edges(n, a, b, w=w, labels=labels, name=f"chunglu{n}")
+    return from_edges(n, a, b, w=w, labels=labels, name=f"chunglu{n}", device=device)
 
 
 def batched_sbm(n_graphs: int, n_min: int = 200, n_max: int = 20000, blocks_min: int = 2,

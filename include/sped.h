@@ -352,16 +352,6 @@ sped_status sped_eig_step(const sped_graph *g, const sped_step_opts *opts, void 
 sped_status sped_eig_step_scratch_size(const sped_graph *g, const sped_step_opts *opts, int k,
                                        size_t *bytes);
 
-/* Measurement entry point (not on the solver path): the chain step's access stream without its
- * arithmetic, to compare the step with the rate at which this GPU serves the same random row
- * gathers. X and Y: n x k BF16 blocks (the chain's storage); Y receives, per row, the sum of the
- * gathered rows (whole 16-byte chunks are written, row padding included). mode 0: the rows
- * named by the CSR (col_idx read as the chain step reads it); mode 1: as many rows per node,
- * hashed uniformly from (entry index, seed), no index stream; mode 2: as many consecutive rows
- * r+1, r+2, ... (mod n). Same launch shape as the row-group chain step. */
-sped_status sped_probe_gather(const sped_graph *g, int k, const void *d_X, int ldx, void *d_Y,
-                              int ldy, int mode, uint64_t seed, void *stream);
-
 /* Rayleigh quotients of the Laplacian itself, lambda_i = <v_i, L v_i>/<v_i, v_i>, in FP64
  * (d_out: k doubles). */
 sped_status sped_rayleigh(const sped_graph *g, const void *d_V, sped_dtype v_t, int k, int ld,

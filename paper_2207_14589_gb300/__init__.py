@@ -126,7 +126,6 @@ def lib():
         "sped_set_schedule": [vp, i32, i32],
         "sped_poly_moments": [vp, vp, i32, i32, i32, i32, i32, dbl, dbl, vp, vp, sz, vp],
         "sped_poly_moments_scratch_size": [vp, i32, i32, P(sz)],
-        "sped_probe_gather": [vp, i32, vp, i32, vp, i32, i32, u64, vp],
         "sped_device_status": [vp],
         "sped_test_gram_waits": [ctypes.c_uint32, i32],
         "sped_sample_edges": [vp, u64, ctypes.c_uint32, i64, i32, vp, vp, vp, vp, vp],
@@ -346,18 +345,6 @@ def poly_moments(g: Graph, V, k, n_moments, basis="chebyshev", a=0.0, b=0.0, str
                                    int(n_moments), float(a), float(b), _ptr(out), _ptr(scr),
                                    nb.value, _stream(stream)))
     return out
-
-
-def probe_gather(g: Graph, X, Y, k, mode=0, seed=0, stream=None):
-    """The chain step's gathers without its arithmetic (mode 0: CSR order, 1: hashed rows,
-    2: consecutive rows); X and Y are BF16 blocks, Y receives the per-row sums."""
-    xt, ldx = _block(X, k)
-    yt, ldy = _block(Y, k)
-    if xt != BF16 or yt != BF16:
-        raise TypeError("probe_gather works on bfloat16 blocks")
-    _check(lib().sped_probe_gather(g.handle, k, _ptr(X), ldx, _ptr(Y), ldy, int(mode), int(seed),
-                                   _stream(stream)))
-    return Y
 
 
 def sample_edges(g: Graph, seed, step, count, stratified=False, stream=None):

@@ -63,9 +63,30 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
         os.replace(tmp, LIB)
+    _build_probe(force)
     if verbose:
         print(LIB)
     return LIB
+
+
+PROBE_DIR = os.path.join(HERE, "probe")
+PROBE_LIB = os.path.join(PROBE_DIR, "libsped_probe.so")
+
+
+def _build_probe(force: bool = False) -> str:
+    """The benchmark's measurement library (gather-rate probe), one translation unit, kept out
+    of libsped."""
+    src = os.path.join(PROBE_DIR, "gather_probe.cu")
+    deps = [src, os.path.join(PROBE_DIR, "sped_probe.h")]
+    if force or _stale(PROBE_LIB, deps):
+        tmp = PROBE_LIB + f".{os.getpid()}.tmp"
+        cmd = [_nvcc(), "-shared", "-o", tmp, src] + ARCH + [
+            "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O3", "-I", PROBE_DIR]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, PROBE_LIB)
+    return PROBE_LIB
 
 
 if __name__ == "__main__":
