@@ -1,25 +1,24 @@
 // Tall-skinny Gram G = X^T X, X = [A B] (n x K2), on the 5th-generation tensor cores.
 //
-// Each F32 value x is split into BF16 pieces x = h + m + l (h = bf16(x), m = bf16(x - h),
-// l = bf16(x - h - m)); products of BF16 pieces are exact in F32, so the nine piece products
+// Each F32 value x is split into BF16 pieces x = h + m + l: h is the top 16 bits of x (a BF16
+// value, truncated), m the top 16 bits of x - h, l = x - h - m (exactly a BF16 value: after two
+// truncations at most 8 significant bits are left); every remainder is exact in F32, so the
+// split is exact, and products of BF16 pieces are exact in F32, so the nine piece products
 // recover x_i x_j to F32 accuracy. The pieces are stacked as S*K2 <= 128 operand rows (S = 3
 // for F32 inputs, 1 for BF16) and one tcgen05.mma (M = N = 128, K = 16 graph rows, kind::f16
 // with BF16 operands, F32 accumulator in tensor memory) consumes 16 rows; the same
 // shared-memory tile is both operands because G is a Gram matrix.
 //
-// Pipeline per CTA (one per SM, tiles of 128 graph rows taken round-robin):
-//  * thread 0 keeps NRAW - 1 tiles of raw rows in flight: one bulk copy (cp.async.bulk) of the
-//    tile's contiguous rows of A and one of B into a raw stage, completion counted in bytes on
-//    the stage's mbarrier; a stage is refilled once every warp has arrived on its "empty"
-//    barrier;
-//  * all warps split the raw stage into the K-major core-matrix layout of an operand stage
-//    (two operand stages, one per MMA batch in flight);
-//  * thread 0 issues the tile's 8 MMAs and a tcgen05.commit to the operand stage's mbarrier;
-//  * every 4 tiles the accumulator is read back and added to double-float (TwoSum) running
-//    sums that live in spare tensor-memory columns (the accumulator uses 128 of 512), bounding
-//    each F32 accumulation to 512 rows.
-// At the end the running sums go to shared memory, the nine piece blocks are combined per
-// (i, j) and the CTA writes an F64 partial; a second kernel sums the partials in a fixed order.
+// One persistent CTA per SM takes tiles of 128 graph rows round-robin through a warp-
+// specialised pipeline (see k_gram_ws): a producer warp keeps a ring of raw tiles filled with
+// bulk copies (cp.async.bulk, completion counted in bytes on each stage's mbarrier), splitter
+// warps turn a raw tile into the K-major core-matrix layout of an operand stage, one thread
+// issues the tile's 8 MMAs into one of two accumulators in tensor memory and commits them to
+// the stage's mbarrier, and every 4 tiles (512 rows, bounding each F32 accumulation run) folder
+// warps add the full accumulator to double-float (TwoSum) running sums kept in the other half
+// of tensor memory while the MMAs fill the second accumulator. At the end the running sums go
+// to shared memory, the nine piece blocks are combined per (i, j) and the CTA writes an F64
+// partial; a second kernel sums the partials in a fixed order (deterministic).
 //
 // Shared-memory operand layout (no swizzle, K-major): per 16-row slice a 128 x 16 BF16 block
 // made of 8 x 8 core matrices (128 contiguous bytes each); core matrix (g = m/8, h = k/8) at
@@ -37,36 +36,15 @@
 
 namespace sped {
 
-constexpr int TC_THREADS = 640;       // 20 warps: one split unit per thread at k = 20 (K2 = 40)
-constexpr int TC_WARPS = TC_THREADS / 32;
 constexpr int TC_RAW_CHUNKS = 2048;   // 16-byte chunks of one tile of A and B at most
-constexpr int TC_RAW_BYTES = TC_RAW_CHUNKS * 16;
-constexpr int TC_NRAW = 3;            // raw stages: two tiles' copies in flight during a split
-constexpr int TC_FOLD_WARPS = 16;     // warps that read tensor memory (4 per TMEM lane quarter)
 constexpr int TC_TILE = 128;          // graph rows per tile
 constexpr int TC_SLICES = TC_TILE / 16;
 constexpr int TC_SLICE_BYTES = 128 * 16 * 2;
 constexpr int TC_STAGE_BYTES = TC_SLICES * TC_SLICE_BYTES;  // 32 KB
 constexpr int TC_FLUSH = 4;           // tiles per F32 accumulation run
 constexpr int TC_COLS = 128;          // accumulator columns (N)
-constexpr int TC_HI = 128, TC_LO = 256;  // tensor-memory columns of the running sums
 constexpr int TC_TMEM_COLS = 512;     // allocation (power of two >= 384)
 constexpr uint32_t TC_WAIT_LIMIT = 1u << 22;
-
-struct TcSmem {
-    // the operand stages and the raw stages are contiguous: at the end they hold the running
-    // sums read out of tensor memory (2 x 64 KB)
-    alignas(1024) unsigned char stage[2][TC_STAGE_BYTES];
-    alignas(128) unsigned char raw[TC_NRAW][TC_RAW_BYTES];
-    alignas(8) uint64_t mma_bar[2];
-    alignas(8) uint64_t full_bar[TC_NRAW];
-    alignas(8) uint64_t empty_bar[TC_NRAW];
-    uint32_t tmem_base;
-    int timed_out;
-    int wait_ok;
-};
-static_assert(sizeof(TcSmem::stage) + sizeof(TcSmem::raw) >= 2 * 128 * 128 * sizeof(float),
-              "final staging of the running sums");
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -177,30 +155,120 @@ __device__ __forceinline__ void two_sum(float &s, float &e, float x) {
     s = t;
 }
 
+// ---------------------------------------------------------------------------------------
+// Warp-specialised version: every stage of the pipeline has its own warps and mbarriers, so no
+// warp waits for work it does not consume.
+//   warp 0       producer: lane 0 keeps the raw ring full with bulk copies (nraw stages);
+//   warps 1..NS  splitters: raw stage -> BF16 pieces in an operand stage;
+//   warp NS+1    MMA: lane 0 issues the tile's 8 MMAs into one of two accumulators in tensor
+//                memory and commits to the operand stage's "empty" barrier (and, every
+//                TC_FLUSH tiles, to the accumulator's "full" barrier);
+//   warps NS+2.. folders (one per tensor-memory lane quarter): add a full accumulator to the
+//                double-float running sums while the MMA warp fills the other one.
+// Tensor memory: accumulators in columns [0, 128) and [128, 256), running sums hi / lo in
+// [256, 384) and [384, 512). Every wait is bounded and also gives up once another warp has
+// given up; the CTA then waits (bounded) for its copies and MMAs in flight, frees its tensor
+// memory, writes NaN partials and sets the device status word.
+// ---------------------------------------------------------------------------------------
+constexpr int WS_NS = 24;                         // splitter warps
+constexpr int WS_MMA_WARP = 1 + WS_NS;
+constexpr int WS_FOLD0 = WS_MMA_WARP + 1;         // first of the four folder warps
+constexpr int WS_WARPS = WS_FOLD0 + 4;
+constexpr int WS_THREADS = WS_WARPS * 32;
+constexpr int WS_MAXRAW = 8;
+constexpr int WS_NOP = 4;                         // operand stages
+constexpr int WS_RAW_BYTES = 88 * 1024;
+constexpr uint32_t WS_HI = 256, WS_LO = 384;
+
+struct WsSmem {
+    // operand stages and raw ring are contiguous: at the end they hold the running sums
+    alignas(1024) unsigned char stage[WS_NOP][TC_STAGE_BYTES];
+    alignas(1024) unsigned char raw[WS_RAW_BYTES];
+    alignas(8) uint64_t raw_full[WS_MAXRAW];
+    alignas(8) uint64_t raw_empty[WS_MAXRAW];
+    alignas(8) uint64_t op_full[WS_NOP];
+    alignas(8) uint64_t op_empty[WS_NOP];
+    alignas(8) uint64_t acc_full[2];
+    alignas(8) uint64_t acc_empty[2];
+    uint32_t tmem_base;
+    int abort;
+    int timed_out;
+};
+static_assert(sizeof(WsSmem::stage) + sizeof(WsSmem::raw) >= 2 * 128 * 128 * sizeof(float),
+              "final staging of the running sums");
+
+// one potentially blocking probe of the phase: the hardware suspends the thread until the phase
+// completes or a time limit of its own passes (no issue slots spent spinning)
+__device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// bounded wait (at most `limit` probes and about two seconds) that also gives up when another
+// warp of the CTA has given up
+__device__ __forceinline__ bool ws_wait(uint32_t mbar, uint32_t parity, uint32_t limit,
+                                        volatile int *abort) {
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 0; it < limit; ++it) {
+        if (mbar_try(mbar, parity)) return true;
+        if (*abort) return false;
+        if (global_ns() - t0 > 2000000000ull) break;
+    }
+    *abort = 1;
+    return false;
+}
+
 template <typename Ta, typename Tb, int S>
-__global__ void __launch_bounds__(TC_THREADS, 1)
-k_gram_tc(int64_t n, const Ta *__restrict__ A, int lda, int ka, const Tb *__restrict__ B, int ldb,
+__global__ void __launch_bounds__(WS_THREADS, 1)
+k_gram_ws(int64_t n, const Ta *__restrict__ A, int lda, int ka, const Tb *__restrict__ B, int ldb,
           int kb, double *__restrict__ partial, uint32_t wait_limit, int skip_fills) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    TcSmem &sm = *reinterpret_cast<TcSmem *>(
+    WsSmem &sm = *reinterpret_cast<WsSmem *>(
         smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023));
     const int t = threadIdx.x;
     const int warp = t >> 5, lane = t & 31;
     const int K2 = ka + kb;
-    const int c_first = t % K2, g_first = t / K2;                 // this thread's first split unit
-    const int c_step = TC_THREADS % K2, g_step = TC_THREADS / K2;  // and the stride between units
     const int64_t ntiles = (n + TC_TILE - 1) / TC_TILE;
     const int64_t my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const int64_t n_groups = (my_tiles + TC_FLUSH - 1) / TC_FLUSH;
+    const uint32_t tile_max = (uint32_t)TC_TILE * ((uint32_t)lda * (uint32_t)sizeof(Ta) +
+                                                   (kb ? (uint32_t)ldb * (uint32_t)sizeof(Tb) : 0u));
+    const uint32_t stage_bytes = (tile_max + 127u) & ~127u;
+    int nraw = (int)(WS_RAW_BYTES / stage_bytes);
+    if (nraw > WS_MAXRAW) nraw = WS_MAXRAW;
+    volatile int *abort = &sm.abort;
     // ---- set-up: zero the operand stages (rows past S K2 stay zero), barriers, tensor memory
-    for (int e = t; e < 2 * TC_STAGE_BYTES / 16; e += TC_THREADS)
+    for (int e = t; e < WS_NOP * TC_STAGE_BYTES / 16; e += WS_THREADS)
         reinterpret_cast<uint4 *>(&sm.stage[0][0])[e] = make_uint4(0, 0, 0, 0);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // zeros seen by the MMAs
     if (t == 0) {
-        for (int i = 0; i < 2; ++i) mbar_init(smem_u32(&sm.mma_bar[i]), 1);
-        for (int i = 0; i < TC_NRAW; ++i) {
-            mbar_init(smem_u32(&sm.full_bar[i]), 1);
-            mbar_init(smem_u32(&sm.empty_bar[i]), TC_WARPS);
+        for (int i = 0; i < WS_MAXRAW; ++i) {
+            mbar_init(smem_u32(&sm.raw_full[i]), 1);
+            mbar_init(smem_u32(&sm.raw_empty[i]), WS_NS);
+        }
+        for (int i = 0; i < WS_NOP; ++i) {
+            mbar_init(smem_u32(&sm.op_full[i]), WS_NS);
+            mbar_init(smem_u32(&sm.op_empty[i]), 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(smem_u32(&sm.acc_full[i]), 1);
+            mbar_init(smem_u32(&sm.acc_empty[i]), 4);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        sm.abort = 0;
         sm.timed_out = 0;
     }
     if (warp == 0) {
@@ -213,83 +281,51 @@ k_gram_tc(int64_t n, const Ta *__restrict__ A, int lda, int ka, const Tb *__rest
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = sm.tmem_base;
-    // warp w < 16 owns TMEM lane quarter w % 4 and accumulator columns [32 (w / 4), +32)
-    const bool folder = warp < TC_FOLD_WARPS;
-    const uint32_t lane_q = (uint32_t)((warp & 3) * 32) << 16;
-    const int col0 = (warp >> 2) * 32;
-    if (folder) {  // running sums start at zero
-        uint32_t z[16];
-#pragma unroll
-        for (int q = 0; q < 16; ++q) z[q] = 0u;
-#pragma unroll
-        for (int h = 0; h < 32; h += 16) {
-            tmem_st16(tmem + lane_q + (uint32_t)(TC_HI + col0 + h), z);
-            tmem_st16(tmem + lane_q + (uint32_t)(TC_LO + col0 + h), z);
+    int64_t issued = 0;      // producer (warp 0, lane 0): fills issued
+    int64_t mma_issued = 0;  // MMA warp, lane 0: tiles whose MMAs were issued
+
+    if (warp == 0) {
+        // ---- producer
+        if (lane == 0 && !skip_fills) {
+            for (int64_t f = 0; f < my_tiles; ++f) {
+                const int rs = (int)(f % nraw);
+                if (f >= nraw && !ws_wait(smem_u32(&sm.raw_empty[rs]),
+                                          (uint32_t)(((f / nraw) - 1) & 1), wait_limit, abort))
+                    break;
+                const int64_t r0 = (blockIdx.x + f * gridDim.x) * (int64_t)TC_TILE;
+                const int rows = (int)(n - r0 < TC_TILE ? n - r0 : TC_TILE);
+                const uint32_t ba = (uint32_t)((size_t)rows * lda * sizeof(Ta));
+                const uint32_t bb = kb ? (uint32_t)((size_t)rows * ldb * sizeof(Tb)) : 0u;
+                const uint32_t bar = smem_u32(&sm.raw_full[rs]);
+                const uint32_t dst = smem_u32(sm.raw) + (uint32_t)rs * stage_bytes;
+                mbar_arrive_expect_tx(bar, ba + bb);
+                bulk_g2s(dst, A + r0 * lda, ba, bar);
+                if (bb) bulk_g2s(dst + ba, B + r0 * ldb, bb, bar);
+                issued = f + 1;
+            }
         }
-        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-    }
-    const uint32_t idesc = tc_idesc();
-    // raw tile loads (thread 0): fill number f of raw stage f % NRAW holds this CTA's tile f
-    int64_t issued = 0;
-    auto issue = [&]() {  // next fill, once its stage has been released by every warp
-        const int64_t f = issued;
-        if (f >= my_tiles) return true;
-        if (skip_fills) return true;  // test of the timeout path: nothing is ever in flight
-        const int rs = (int)(f % TC_NRAW);
-        if (f >= TC_NRAW &&
-            !mbar_wait(smem_u32(&sm.empty_bar[rs]), (uint32_t)(((f / TC_NRAW) - 1) & 1), wait_limit))
-            return false;
-        const int64_t r0 = (blockIdx.x + f * gridDim.x) * (int64_t)TC_TILE;
-        const int rows = (int)(n - r0 < TC_TILE ? n - r0 : TC_TILE);
-        const uint32_t ba = (uint32_t)((size_t)rows * lda * sizeof(Ta));
-        const uint32_t bb = (uint32_t)((size_t)rows * ldb * sizeof(Tb));
-        const uint32_t bar = smem_u32(&sm.full_bar[rs]);
-        mbar_arrive_expect_tx(bar, ba + bb);
-        bulk_g2s(smem_u32(sm.raw[rs]), A + r0 * lda, ba, bar);
-        if (bb) bulk_g2s(smem_u32(sm.raw[rs]) + ba, B + r0 * ldb, bb, bar);
-        ++issued;
-        return true;
-    };
-    if (t == 0) {
-        for (int f = 0; f < TC_NRAW - 1; ++f)
-            if (!issue()) sm.timed_out = 1;
-    }
-    uint32_t mma_par[2] = {0, 0};
-    bool pending[2] = {false, false};
-    bool fresh = true;  // next MMA overwrites the accumulator
-    bool ok = true;
-    for (int64_t it = 0; it < my_tiles && ok; ++it) {
-        const int64_t tile = blockIdx.x + it * gridDim.x;
-        const int st = (int)(it & 1);
-        const int rs = (int)(it % TC_NRAW);
-        // ---- thread 0: keep NRAW - 1 fills ahead, then wait for this tile's rows and for the
-        // MMAs that last read this operand stage; every thread gets the same answer
-        if (t == 0) {
-            bool good = sm.timed_out == 0;
-            if (good && issued < my_tiles && !issue()) good = false;
-            if (good && !mbar_wait(smem_u32(&sm.full_bar[rs]), (uint32_t)((it / TC_NRAW) & 1), wait_limit))
-                good = false;
-            if (good && pending[st] && !mbar_wait(smem_u32(&sm.mma_bar[st]), mma_par[st], wait_limit))
-                good = false;
-            if (!good) sm.timed_out = 1;
-            sm.wait_ok = good ? 1 : 0;
-        }
-        __syncthreads();
-        ok = sm.wait_ok != 0;
-        if (!ok) break;
-        if (pending[st]) {
-            mma_par[st] ^= 1;
-            pending[st] = false;
-        }
-        // ---- split: unit (c, g) is column c of [A B] over graph rows 8g .. 8g+7 (zero past the
-        // end); each of its S BF16 pieces is 8 consecutive K elements, i.e. one 16-byte row of
-        // a core matrix (operand row m = s K2 + c, K half g & 1 of slice g / 2)
-        const int64_t r0 = tile * TC_TILE;
-        const int rows = (int)(n - r0 < TC_TILE ? n - r0 : TC_TILE);
-        {
-            const Ta *ra = reinterpret_cast<const Ta *>(sm.raw[rs]);
-            const Tb *rb = reinterpret_cast<const Tb *>(sm.raw[rs] + (size_t)rows * lda * sizeof(Ta));
-            // unit uu = g K2 + c, advanced by TC_THREADS without a division per unit
+    } else if (warp <= WS_NS) {
+        // ---- splitters: unit (c, g) is column c of [A B] over graph rows 8g .. 8g+7 of the
+        // tile; each of its S BF16 pieces is one 16-byte row of a core matrix (operand row
+        // m = s K2 + c, K half g & 1 of slice g / 2)
+        const int st = t - 32;
+        constexpr int NT = WS_NS * 32;
+        const int c_first = st % K2, g_first = st / K2;
+        const int c_step = NT % K2, g_step = NT / K2;
+        for (int64_t it = 0; it < my_tiles; ++it) {
+            const int rs = (int)(it % nraw);
+            const int o = (int)(it % WS_NOP);
+            bool ok = ws_wait(smem_u32(&sm.raw_full[rs]), (uint32_t)((it / nraw) & 1), wait_limit,
+                              abort);
+            if (ok && it >= WS_NOP)
+                ok = ws_wait(smem_u32(&sm.op_empty[o]), (uint32_t)(((it / WS_NOP) - 1) & 1),
+                             wait_limit, abort);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            const int64_t r0 = (blockIdx.x + it * gridDim.x) * (int64_t)TC_TILE;
+            const int rows = (int)(n - r0 < TC_TILE ? n - r0 : TC_TILE);
+            const unsigned char *raw = sm.raw + (size_t)rs * stage_bytes;
+            const Ta *ra = reinterpret_cast<const Ta *>(raw);
+            const Tb *rb = reinterpret_cast<const Tb *>(raw + (size_t)rows * lda * sizeof(Ta));
             int c = c_first, g = g_first;
             for (; g < TC_TILE / 8; c += c_step, g += g_step) {
                 if (c >= K2) {
@@ -298,24 +334,31 @@ k_gram_tc(int64_t n, const Ta *__restrict__ A, int lda, int ka, const Tb *__rest
                     if (g >= TC_TILE / 8) break;
                 }
                 float x[8];
+                const int r0 = g * 8;
+                if (c < ka) {
 #pragma unroll
-                for (int rr = 0; rr < 8; ++rr) {
-                    const int row = g * 8 + rr;
-                    x[rr] = row >= rows ? 0.f
-                            : c < ka    ? cvt<float>(ra[row * lda + c])
-                                        : cvt<float>(rb[row * ldb + (c - ka)]);
+                    for (int rr = 0; rr < 8; ++rr)
+                        x[rr] = r0 + rr < rows ? cvt<float>(ra[(r0 + rr) * lda + c]) : 0.f;
+                } else {
+#pragma unroll
+                    for (int rr = 0; rr < 8; ++rr)
+                        x[rr] = r0 + rr < rows ? cvt<float>(rb[(r0 + rr) * ldb + (c - ka)]) : 0.f;
                 }
-                unsigned char *slice = sm.stage[st] + (g >> 1) * TC_SLICE_BYTES + (g & 1) * 128;
+                unsigned char *slice = sm.stage[o] + (g >> 1) * TC_SLICE_BYTES + (g & 1) * 128;
 #pragma unroll
                 for (int s = 0; s < S; ++s) {
+                    // piece s: the top 16 bits (a BF16 value, truncated) of what is left; the
+                    // remainder x - piece is exact in F32, and after three pieces nothing is
+                    // left, so x = h + m + l exactly
                     uint32_t w[4];
 #pragma unroll
                     for (int p2 = 0; p2 < 4; ++p2) {
-                        const __nv_bfloat162 h2 = __floats2bfloat162_rn(x[2 * p2], x[2 * p2 + 1]);
-                        w[p2] = *reinterpret_cast<const uint32_t *>(&h2);
-                        if (s + 1 < S) {  // the rounding residual is exact in F32
-                            x[2 * p2] -= __low2float(h2);
-                            x[2 * p2 + 1] -= __high2float(h2);
+                        const uint32_t a = __float_as_uint(x[2 * p2]) & 0xffff0000u;
+                        const uint32_t b = __float_as_uint(x[2 * p2 + 1]) & 0xffff0000u;
+                        w[p2] = __byte_perm(a, b, 0x7632);
+                        if (s + 1 < S) {
+                            x[2 * p2] -= __uint_as_float(a);
+                            x[2 * p2 + 1] -= __uint_as_float(b);
                         }
                     }
                     const int m = s * K2 + c;
@@ -323,92 +366,131 @@ k_gram_tc(int64_t n, const Ta *__restrict__ A, int lda, int ka, const Tb *__rest
                         make_uint4(w[0], w[1], w[2], w[3]);
                 }
             }
-        }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(&sm.empty_bar[rs]));  // raw stage may be refilled
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (t == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            const uint32_t sbase = smem_u32(sm.stage[st]);
-#pragma unroll
-            for (int s = 0; s < TC_SLICES; ++s) {
-                const uint64_t d = tc_desc(sbase + s * TC_SLICE_BYTES);
-                tc_mma(tmem, d, d, idesc, (fresh && s == 0) ? 0u : 1u);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(smem_u32(&sm.raw_empty[rs]));  // raw stage may be refilled
+                mbar_arrive(smem_u32(&sm.op_full[o]));     // operand stage ready for the MMAs
             }
-            tc_commit(smem_u32(&sm.mma_bar[st]));
         }
-        fresh = false;
-        pending[st] = true;
-        if ((it + 1) % TC_FLUSH == 0 || it + 1 == my_tiles) {
-            // ---- fold the accumulator into the double-float running sums in tensor memory
-            if (t == 0) {
-                const bool good = mbar_wait(smem_u32(&sm.mma_bar[st]), mma_par[st], wait_limit);
-                if (!good) sm.timed_out = 1;
-                sm.wait_ok = good ? 1 : 0;
-            }
-            __syncthreads();
-            ok = sm.wait_ok != 0;
-            if (!ok) break;
-            mma_par[st] ^= 1;
-            pending[st] = false;
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            if (folder) {
-#pragma unroll 1
-                for (int h = 0; h < 32; h += 16) {
-                    uint32_t v[16], hi[16], lo[16];
-                    tmem_ld16(tmem + lane_q + (uint32_t)(col0 + h), v);
-                    tmem_ld16(tmem + lane_q + (uint32_t)(TC_HI + col0 + h), hi);
-                    tmem_ld16(tmem + lane_q + (uint32_t)(TC_LO + col0 + h), lo);
-                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    } else if (warp == WS_MMA_WARP) {
+        // ---- MMA issue
+        if (lane == 0) {
+            const uint32_t idesc = tc_idesc();
+            int b = 0, in_group = 0;
+            int64_t g = 0;
+            for (int64_t it = 0; it < my_tiles; ++it) {
+                const int o = (int)(it % WS_NOP);
+                if (in_group == 0 && g >= 2 &&
+                    !ws_wait(smem_u32(&sm.acc_empty[b]), (uint32_t)(((g >> 1) - 1) & 1),
+                             wait_limit, abort))
+                    break;
+                if (!ws_wait(smem_u32(&sm.op_full[o]), (uint32_t)((it / WS_NOP) & 1), wait_limit,
+                             abort))
+                    break;
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const uint32_t sbase = smem_u32(sm.stage[o]);
 #pragma unroll
-                    for (int q = 0; q < 16; ++q) {
-                        float sh = __uint_as_float(hi[q]), el = __uint_as_float(lo[q]);
-                        two_sum(sh, el, __uint_as_float(v[q]));
-                        hi[q] = __float_as_uint(sh);
-                        lo[q] = __float_as_uint(el);
-                    }
-                    tmem_st16(tmem + lane_q + (uint32_t)(TC_HI + col0 + h), hi);
-                    tmem_st16(tmem + lane_q + (uint32_t)(TC_LO + col0 + h), lo);
+                for (int s = 0; s < TC_SLICES; ++s) {
+                    const uint64_t d = tc_desc(sbase + s * TC_SLICE_BYTES);
+                    tc_mma(tmem + (uint32_t)(b * TC_COLS), d, d, idesc,
+                           (in_group == 0 && s == 0) ? 0u : 1u);
                 }
-                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                tc_commit(smem_u32(&sm.op_empty[o]));
+                mma_issued = it + 1;
+                if (++in_group == TC_FLUSH || it + 1 == my_tiles) {
+                    tc_commit(smem_u32(&sm.acc_full[b]));
+                    b ^= 1;
+                    in_group = 0;
+                    ++g;
+                }
             }
+        }
+    } else {
+        // ---- folders: warp w owns tensor-memory lanes 32 (w % 4) .. +32, all 128 columns
+        const uint32_t lane_q = (uint32_t)((warp & 3) * 32) << 16;
+        {
+            uint32_t z[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) z[q] = 0u;
+#pragma unroll 1
+            for (int h = 0; h < TC_COLS; h += 16) {
+                tmem_st16(tmem + lane_q + WS_HI + (uint32_t)h, z);
+                tmem_st16(tmem + lane_q + WS_LO + (uint32_t)h, z);
+            }
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        }
+        for (int64_t g = 0; g < n_groups; ++g) {
+            const int b = (int)(g & 1);
+            const bool ok = ws_wait(smem_u32(&sm.acc_full[b]), (uint32_t)((g >> 1) & 1),
+                                    wait_limit, abort);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll 1
+            for (int h = 0; h < TC_COLS; h += 16) {
+                uint32_t v[16], hi[16], lo[16];
+                tmem_ld16(tmem + lane_q + (uint32_t)(b * TC_COLS + h), v);
+                tmem_ld16(tmem + lane_q + WS_HI + (uint32_t)h, hi);
+                tmem_ld16(tmem + lane_q + WS_LO + (uint32_t)h, lo);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    float sh = __uint_as_float(hi[q]), el = __uint_as_float(lo[q]);
+                    two_sum(sh, el, __uint_as_float(v[q]));
+                    hi[q] = __float_as_uint(sh);
+                    lo[q] = __float_as_uint(el);
+                }
+                tmem_st16(tmem + lane_q + WS_HI + (uint32_t)h, hi);
+                tmem_st16(tmem + lane_q + WS_LO + (uint32_t)h, lo);
+            }
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
             asm volatile("tcgen05.fence::before_thread_sync;");
-            fresh = true;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&sm.acc_empty[b]));  // accumulator b free
         }
     }
-    // ---- on a timeout, wait (bounded) for whatever is still in flight: MMAs, raw copies
-    if (t == 0) {
-        if (!ok) sm.timed_out = 1;
-        for (int s = 0; s < 2; ++s)
-            if (pending[s] && !mbar_wait(smem_u32(&sm.mma_bar[s]), mma_par[s], wait_limit)) sm.timed_out = 2;
-        // fills issued but not consumed by the loop (only after a timeout)
-        if (!ok)
-            for (int64_t f = 0; f < issued; ++f)
-                if (!mbar_wait(smem_u32(&sm.full_bar[f % TC_NRAW]), (uint32_t)((f / TC_NRAW) & 1),
+    __syncwarp();
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    // ---- after a wait gave up: wait (bounded) for the copies and MMAs still in flight
+    if (sm.abort) {
+        if (warp == 0 && lane == 0) {
+            int bad = 1;
+            for (int64_t f = issued - nraw > 0 ? issued - nraw : 0; f < issued; ++f)
+                if (!mbar_wait(smem_u32(&sm.raw_full[f % nraw]), (uint32_t)((f / nraw) & 1),
                                wait_limit))
-                    sm.timed_out = 2;
+                    bad = 2;
+            if (bad == 2) sm.timed_out = 2;
+        }
+        if (warp == WS_MMA_WARP && lane == 0 && mma_issued > 0) {
+            const int64_t it = mma_issued - 1;
+            if (!mbar_wait(smem_u32(&sm.op_empty[it % WS_NOP]), (uint32_t)((it / WS_NOP) & 1),
+                           wait_limit))
+                sm.timed_out = 2;
+        }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
+    const int bad = sm.abort ? (sm.timed_out == 2 ? 2 : 1) : 0;
+    if (bad && t == 0) atomicOr(&g_device_status, 1u);
     // the running sums to shared memory ([n][m] layout), unless copies may still be landing
     float *fin_hi = reinterpret_cast<float *>(&sm.stage[0][0]);
     float *fin_lo = fin_hi + 128 * 128;
-    const int bad = sm.timed_out;
-    if (bad && t == 0) atomicOr(&g_device_status, 1u);
-    if (bad != 2 && folder) {
+    if (bad != 2 && warp >= WS_FOLD0) {
+        const uint32_t lane_q = (uint32_t)((warp & 3) * 32) << 16;
+        const int m = (warp & 3) * 32 + lane;
 #pragma unroll 1
-        for (int h = 0; h < 32; h += 16) {
+        for (int h = 0; h < TC_COLS; h += 16) {
             uint32_t hi[16], lo[16];
-            tmem_ld16(tmem + lane_q + (uint32_t)(TC_HI + col0 + h), hi);
-            tmem_ld16(tmem + lane_q + (uint32_t)(TC_LO + col0 + h), lo);
+            tmem_ld16(tmem + lane_q + WS_HI + (uint32_t)h, hi);
+            tmem_ld16(tmem + lane_q + WS_LO + (uint32_t)h, lo);
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            const int m = (warp & 3) * 32 + lane;
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
-                fin_hi[(col0 + h + q) * 128 + m] = __uint_as_float(hi[q]);
-                fin_lo[(col0 + h + q) * 128 + m] = __uint_as_float(lo[q]);
+                fin_hi[(h + q) * 128 + m] = __uint_as_float(hi[q]);
+                fin_lo[(h + q) * 128 + m] = __uint_as_float(lo[q]);
             }
         }
     }
@@ -420,8 +502,8 @@ k_gram_tc(int64_t n, const Ta *__restrict__ A, int lda, int ka, const Tb *__rest
                      "r"(TC_TMEM_COLS));
     // ---- combine the S x S piece blocks: G[i][j] = sum_{a,b} D[a K2 + i][b K2 + j], i <= j
     double *out = partial + (int64_t)blockIdx.x * K2 * K2;
-    for (int e = t; e < K2 * K2; e += TC_THREADS) {
-        const int i = e / K2, j = e % K2;
+    for (int e = t; e < K2 * K2; e += WS_THREADS) {
+        const int j = e / K2, i = e % K2;  // consecutive threads read consecutive m = a K2 + i
         if (i > j) continue;
         double v = NAN;
         if (!bad) {
@@ -429,8 +511,8 @@ k_gram_tc(int64_t n, const Ta *__restrict__ A, int lda, int ka, const Tb *__rest
 #pragma unroll
             for (int a = 0; a < S; ++a)
 #pragma unroll
-                for (int b = 0; b < S; ++b) {
-                    const int idx = (b * K2 + j) * 128 + (a * K2 + i);
+                for (int b2 = 0; b2 < S; ++b2) {
+                    const int idx = (b2 * K2 + j) * 128 + (a * K2 + i);
                     two_sum(s, err, fin_hi[idx]);
                     err += fin_lo[idx];
                 }
@@ -441,9 +523,9 @@ k_gram_tc(int64_t n, const Ta *__restrict__ A, int lda, int ka, const Tb *__rest
     }
 }
 
-// G[e] = sum over CTAs of partial[c][e]: a block per 32 outputs, 8 thread groups over the
-// partials, then a fixed-order sum of the 8 group totals (deterministic)
-constexpr int RED_OUT = 32, RED_GROUPS = 8;
+// G[e] = sum over CTAs of partial[c][e]: a block per 32 outputs, 32 thread groups over the
+// partials, then a fixed-order sum of the 32 group totals (deterministic)
+constexpr int RED_OUT = 32, RED_GROUPS = 32;
 __global__ void __launch_bounds__(RED_OUT *RED_GROUPS)
 k_gram_tc_reduce(const double *__restrict__ partial, int nparts, int K2, double *__restrict__ G) {
     __shared__ double sm[RED_GROUPS][RED_OUT];
@@ -451,8 +533,20 @@ k_gram_tc_reduce(const double *__restrict__ partial, int nparts, int K2, double 
     const int e = blockIdx.x * RED_OUT + o;
     const int tot = K2 * K2;
     double s = 0.0;
-    if (e < tot)
-        for (int c = grp; c < nparts; c += RED_GROUPS) s += partial[(int64_t)c * tot + e];
+    if (e < tot) {
+        // a group's partials (grp, grp + 32, ...) are loaded together, then added in order
+        constexpr int B = 8;
+        for (int c0 = grp; c0 < nparts; c0 += B * RED_GROUPS) {
+            double v[B];
+#pragma unroll
+            for (int q = 0; q < B; ++q) {
+                const int c = c0 + q * RED_GROUPS;
+                v[q] = c < nparts ? partial[(int64_t)c * tot + e] : 0.0;
+            }
+#pragma unroll
+            for (int q = 0; q < B; ++q) s += v[q];
+        }
+    }
     sm[grp][o] = s;
     __syncthreads();
     if (grp == 0 && e < tot) {
@@ -498,14 +592,13 @@ static std::atomic<int> g_tc_skip_fills{0};
 template <typename Ta, typename Tb, int S>
 static sped_status run_tc(int64_t n, const void *A, int lda, int ka, const void *B, int ldb, int kb,
                           double *G, double *partial, int ctas, cudaStream_t st) {
-    const size_t smem = sizeof(TcSmem) + 1024;
-    auto kern = k_gram_tc<Ta, Tb, S>;
-    SPED_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const uint32_t lim = g_tc_wait_limit.load();
-    kern<<<ctas, TC_THREADS, smem, st>>>(n, (const Ta *)A, lda, ka, (const Tb *)B, ldb, kb,
-                                         partial, lim ? lim : TC_WAIT_LIMIT,
-                                         g_tc_skip_fills.load());
-    SPED_CHECK_LAUNCH("k_gram_tc");
+    const size_t smem = sizeof(WsSmem) + 1024;
+    auto kern = k_gram_ws<Ta, Tb, S>;
+    SPED_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<ctas, WS_THREADS, smem, st>>>(n, (const Ta *)A, lda, ka, (const Tb *)B, ldb, kb, partial,
+                                         lim ? lim : TC_WAIT_LIMIT, g_tc_skip_fills.load());
+    SPED_CHECK_LAUNCH("k_gram_ws");
     const int K2 = ka + kb;
     k_gram_tc_reduce<<<(K2 * K2 + RED_OUT - 1) / RED_OUT, RED_OUT * RED_GROUPS, 0, st>>>(
         partial, ctas, K2, G);
