@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <type_traits>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -153,10 +154,27 @@ template <> struct VecOf<4> { using type = uint32_t; };
 template <> struct VecOf<8> { using type = uint2; };
 template <> struct VecOf<16> { using type = uint4; };
 
+// BF16 -> F32 of the two halves of a 32-bit word: a BF16 value is the top half of the F32 with
+// the same bits, so the conversion is a shift or a mask (exact)
+__device__ __forceinline__ float bf16_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+
 // Read E consecutive elements (E * sizeof(T) bytes, naturally aligned) through the read-only
 // path, converting to the accumulator type.
 template <typename T, int E, typename A>
 __device__ __forceinline__ void load_chunk(const T *__restrict__ p, A (&out)[E]) {
+    if constexpr (std::is_same<T, __nv_bfloat16>::value && std::is_same<A, float>::value &&
+                  E == 8) {
+        // one 16-byte load, converted word by word
+        const uint4 u = __ldg(reinterpret_cast<const uint4 *>(p));
+        const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            out[2 * q] = bf16_lo(w[q]);
+            out[2 * q + 1] = bf16_hi(w[q]);
+        }
+        return;
+    }
     constexpr int BYTES = E * (int)sizeof(T);
     static_assert(BYTES == 4 || BYTES == 8 || BYTES == 16 || BYTES == 32 || BYTES == 64, "chunk");
     constexpr int VB = BYTES < 16 ? BYTES : 16;
