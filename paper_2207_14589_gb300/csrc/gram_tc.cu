@@ -221,10 +221,11 @@ __device__ __forceinline__ uint64_t global_ns() {
 // warp of the CTA has given up
 __device__ __forceinline__ bool ws_wait(uint32_t mbar, uint32_t parity, uint32_t limit,
                                         volatile int *abort) {
+    if (limit > 0 && mbar_try(mbar, parity)) return true;
     const uint64_t t0 = global_ns();
-    for (uint32_t it = 0; it < limit; ++it) {
-        if (mbar_try(mbar, parity)) return true;
+    for (uint32_t it = 1; it < limit; ++it) {
         if (*abort) return false;
+        if (mbar_try(mbar, parity)) return true;
         if (global_ns() - t0 > 2000000000ull) break;
     }
     *abort = 1;
@@ -287,10 +288,11 @@ k_gram_ws(int64_t n, const Ta *__restrict__ A, int lda, int ka, const Tb *__rest
     if (warp == 0) {
         // ---- producer
         if (lane == 0 && !skip_fills) {
+            // stage rs of fill f = f % nraw and its use count u = f / nraw, kept incrementally
+            int rs = 0;
+            uint32_t u = 0;
             for (int64_t f = 0; f < my_tiles; ++f) {
-                const int rs = (int)(f % nraw);
-                if (f >= nraw && !ws_wait(smem_u32(&sm.raw_empty[rs]),
-                                          (uint32_t)(((f / nraw) - 1) & 1), wait_limit, abort))
+                if (u > 0 && !ws_wait(smem_u32(&sm.raw_empty[rs]), (u - 1) & 1u, wait_limit, abort))
                     break;
                 const int64_t r0 = (blockIdx.x + f * gridDim.x) * (int64_t)TC_TILE;
                 const int rows = (int)(n - r0 < TC_TILE ? n - r0 : TC_TILE);
@@ -302,6 +304,10 @@ k_gram_ws(int64_t n, const Ta *__restrict__ A, int lda, int ka, const Tb *__rest
                 bulk_g2s(dst, A + r0 * lda, ba, bar);
                 if (bb) bulk_g2s(dst + ba, B + r0 * ldb, bb, bar);
                 issued = f + 1;
+                if (++rs == nraw) {
+                    rs = 0;
+                    ++u;
+                }
             }
         }
     } else if (warp <= WS_NS) {
@@ -312,11 +318,11 @@ k_gram_ws(int64_t n, const Ta *__restrict__ A, int lda, int ka, const Tb *__rest
         constexpr int NT = WS_NS * 32;
         const int c_first = st % K2, g_first = st / K2;
         const int c_step = NT % K2, g_step = NT / K2;
+        int rs = 0;       // raw stage of tile it (it % nraw) and its use count (it / nraw)
+        uint32_t ru = 0;
         for (int64_t it = 0; it < my_tiles; ++it) {
-            const int rs = (int)(it % nraw);
             const int o = (int)(it % WS_NOP);
-            bool ok = ws_wait(smem_u32(&sm.raw_full[rs]), (uint32_t)((it / nraw) & 1), wait_limit,
-                              abort);
+            bool ok = ws_wait(smem_u32(&sm.raw_full[rs]), ru & 1u, wait_limit, abort);
             if (ok && it >= WS_NOP)
                 ok = ws_wait(smem_u32(&sm.op_empty[o]), (uint32_t)(((it / WS_NOP) - 1) & 1),
                              wait_limit, abort);
@@ -371,6 +377,10 @@ k_gram_ws(int64_t n, const Ta *__restrict__ A, int lda, int ka, const Tb *__rest
             if (lane == 0) {
                 mbar_arrive(smem_u32(&sm.raw_empty[rs]));  // raw stage may be refilled
                 mbar_arrive(smem_u32(&sm.op_full[o]));     // operand stage ready for the MMAs
+            }
+            if (++rs == nraw) {
+                rs = 0;
+                ++ru;
             }
         }
     } else if (warp == WS_MMA_WARP) {
