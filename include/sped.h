@@ -269,7 +269,7 @@ sped_status sped_edge_step(int64_t n, int k, const int32_t *d_a, const int32_t *
 
 /* ------------------------------------------------------------------------------------
  * Gram of a tall-skinny pair: G = [A B]^T [A B], (ka+kb) x (ka+kb) row-major FP64,
- * ka + kb <= 64. d_B may be NULL (kb = 0). Products in F32 for BF16/F32 inputs (exact for
+ * ka + kb <= 80. d_B may be NULL (kb = 0). Products in F32 for BF16/F32 inputs (exact for
  * BF16), accumulated in F32 over short row tiles and in F64 across tiles and CTAs;
  * F64 inputs use F64 throughout. Deterministic (fixed reduction order).
  * ------------------------------------------------------------------------------------ */
@@ -313,7 +313,7 @@ sped_status sped_gram_noalloc(int64_t n, const void *d_A, sped_dtype a_t, int ld
 
 /* ------------------------------------------------------------------------------------
  * One solver step on the graph's operator M (Section 5.1: mu-EG and Oja; Section 3 for the
- * reversal). V (n x k, F32 or F64 master copy, k <= 32) is updated in place:
+ * reversal). V (n x k, F32 or F64 master copy, k <= 40) is updated in place:
  *  mu-EG: delta_i = y_i - sum_{j<i} <v_i,y_j> v_j, r_i = delta_i - <v_i,delta_i> v_i,
  *         v_i <- (v_i + eta r_i)/||.||, all inner products from the Gram [V Y]^T [V Y];
  *  Oja:   V <- (V + eta Y) R^{-1} with R the Cholesky factor of its Gram (eta <= 0: V <- Y R^{-1}).
@@ -365,7 +365,7 @@ sped_status sped_rayleigh_scratch_size(const sped_graph *g, int k, size_t *bytes
  * columns of V W are orthonormal Ritz vectors. d_theta: k doubles; d_W: k x k row-major
  * doubles (W[j*k + i] = coefficient of v_j in Ritz vector i), may be NULL; rotate != 0
  * replaces V by V W in place. When V^T V is not positive definite theta is NaN (and V is left
- * unchanged only if rotate == 0). k <= 32, V F32 or F64. */
+ * unchanged only if rotate == 0). k <= 40, V F32 or F64. */
 sped_status sped_rayleigh_ritz(const sped_graph *g, void *d_V, sped_dtype v_t, int k, int ld,
                                double *d_theta, double *d_W, int rotate, void *d_scratch,
                                size_t scratch_bytes, void *stream);
@@ -498,7 +498,7 @@ sped_status sped_eg_utilities(int k, const double *d_H, int ldh, const double *d
 
 /* Out = A P + B Q for n x k blocks (F32 or F64, type t) and k x k row-major FP64 matrices
  * (Out[r][i] = sum_j A[r][j] P[j][i] + B[r][j] Q[j][i]); d_B may be NULL. Out must not
- * overlap A or B. k <= 32. */
+ * overlap A or B. k <= 40. */
 sped_status sped_block_combine(int64_t n, int k, const void *d_A, int lda, const double *d_P,
                                const void *d_B, int ldb, const double *d_Q, void *d_Out, int ldo,
                                sped_dtype t, void *stream);

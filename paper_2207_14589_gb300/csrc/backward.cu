@@ -18,6 +18,7 @@
 namespace sped {
 
 constexpr int BW_MAXK = 32;
+constexpr int COMBINE_MAXK = 40;  // sped_block_combine (also applies Rayleigh-Ritz rotations)
 
 // one CTA: utilities u, Hbar for weights g (may be NULL: no Hbar), and the detached-parents
 // coefficients S with du_i/dv_i = sum_j y_j S[j][i] (parents v_j, j < i, held fixed)
@@ -114,7 +115,8 @@ static void launch_combine(int64_t n, int k, const T *A, int lda, const double *
     const unsigned nb = (unsigned)((n + 255) / 256);
     if (k <= 8) k_combine<T, 8><<<nb, 256, 0, st>>>(n, k, A, lda, P, B, ldb, Q, Out, ldo);
     else if (k <= 16) k_combine<T, 16><<<nb, 256, 0, st>>>(n, k, A, lda, P, B, ldb, Q, Out, ldo);
-    else k_combine<T, 32><<<nb, 256, 0, st>>>(n, k, A, lda, P, B, ldb, Q, Out, ldo);
+    else if (k <= 32) k_combine<T, 32><<<nb, 256, 0, st>>>(n, k, A, lda, P, B, ldb, Q, Out, ldo);
+    else k_combine<T, 40><<<nb, 256, 0, st>>>(n, k, A, lda, P, B, ldb, Q, Out, ldo);
 }
 
 template <typename T>
@@ -239,7 +241,7 @@ sped_status sped_eg_utilities(int k, const double *d_H, int ldh, const double *d
 sped_status sped_block_combine(int64_t n, int k, const void *d_A, int lda, const double *d_P,
                                const void *d_B, int ldb, const double *d_Q, void *d_Out, int ldo,
                                sped_dtype t, void *stream) {
-    if (n < 0 || k < 1 || k > BW_MAXK || !d_A || !d_P || !d_Out || lda < k || ldo < k ||
+    if (n < 0 || k < 1 || k > COMBINE_MAXK || !d_A || !d_P || !d_Out || lda < k || ldo < k ||
         (d_B && (!d_Q || ldb < k)))
         return fail(SPED_ERR_INVALID_ARG, "block_combine: bad arguments");
     if (t != SPED_F32 && t != SPED_F64) return fail(SPED_ERR_UNSUPPORTED, "block_combine: F32/F64");

@@ -14,7 +14,7 @@ namespace sped {
 constexpr int GRAM_THREADS = 256;
 constexpr int GRAM_TILE = 128;   // rows per shared-memory tile
 constexpr int GRAM_WINDOW = 256; // rows per F32 accumulation window (per worker)
-constexpr int GRAM_MAXK = 64;
+constexpr int GRAM_MAXK = 80;  // 2k for k <= 40 (the 4x4 block pairs fit one CTA's threads)
 
 struct GramShape {
     int K2, KP, nb, P, S, stride;
@@ -157,7 +157,7 @@ size_t gram_scratch(int64_t n, int ka, int kb) {
     int64_t c = 2LL * 256;  // upper bound on CTAs for any device this library supports
     if (tiles < c) c = tiles < 1 ? 1 : tiles;
     const size_t core = sizeof(double) * (size_t)c * sh.P * 16;
-    const size_t tc = (ka + kb) <= 64 ? gram_tc_scratch(n, ka, kb) : 0;  // tensor path (BF16 too)
+    const size_t tc = (ka + kb) <= GRAM_MAXK ? gram_tc_scratch(n, ka, kb) : 0;  // tensor path
     p.add(core > tc ? core : tc);
     return p.total();
 }
@@ -274,6 +274,7 @@ sped_status sped_gram(int64_t n, const void *d_A, sped_dtype a_t, int lda, int k
 namespace sped {
 
 constexpr size_t GRAM_STATIC_DOUBLES = 512 * 1024;  // 4 MiB
+constexpr int GRAM_STATIC_MAXK = 64;                 // columns ka + kb at most
 constexpr int GRAM_STATIC_MAX_DEVICES = 64;
 
 static __device__ __align__(256) double g_gram_static_partials[GRAM_STATIC_DOUBLES];
@@ -311,10 +312,10 @@ extern "C" sped_status sped_gram_noalloc(int64_t n, const void *d_A, sped_dtype 
         return fail(SPED_ERR_INVALID_ARG, "gram_noalloc: B layout");
     SPED_TRY(check_layout(d_A, a_t, ka, lda, "gram_noalloc A"));
     if (kb > 0) SPED_TRY(check_layout(d_B, b_t, kb, ldb, "gram_noalloc B"));
-    if (ka + kb > GRAM_MAXK)
+    if (ka + kb > GRAM_STATIC_MAXK)
         return fail(SPED_ERR_UNSUPPORTED,
                     "gram_noalloc: ka + kb = %d exceeds the maximum of %d columns", ka + kb,
-                    GRAM_MAXK);
+                    GRAM_STATIC_MAXK);
     const GramShape sh = gram_shape(ka, kb);
     const size_t per_cta = (size_t)sh.P * 16;
     if (per_cta > GRAM_STATIC_DOUBLES)

@@ -16,6 +16,8 @@ namespace sped {
 
 constexpr int SMALL_THREADS = 256;
 constexpr int SLD = MAXK + 1;  // row stride of the k x k work arrays (odd: conflict-free columns)
+constexpr size_t SMALL_SMEM = 5 * sizeof(double) * MAXK * SLD;
+constexpr size_t RR_SMEM = 4 * sizeof(double) * MAXK * SLD;
 
 // The k x k stage is FP64 and latency-bound on one SM, so every kernel-level step below spreads
 // its products over all threads and keeps the serial chain short: one rsqrt per Cholesky pivot,
@@ -79,8 +81,11 @@ __device__ void trsv_upper(const double *R, const double *rinv, double *Z, doubl
 // k x k stage. G is (2k x 2k): [P H; H^T Q] with P = V^T V, H = V^T Y, Q = Y^T Y.
 __global__ void __launch_bounds__(SMALL_THREADS)
 k_small(const double *__restrict__ G, int k, double eta, int solver, Coefs *cf, double *stats) {
-    __shared__ double sP[MAXK * SLD], sH[MAXK * SLD], sW[MAXK * SLD], sR[MAXK * SLD],
-        sB[MAXK * SLD], rinv[MAXK], cmu[MAXK];
+    // five k x k work arrays (SMALL_SMEM bytes of dynamic shared memory)
+    extern __shared__ __align__(16) double small_smem[];
+    double *sP = small_smem, *sH = sP + MAXK * SLD, *sW = sH + MAXK * SLD, *sR = sW + MAXK * SLD,
+           *sB = sR + MAXK * SLD;
+    __shared__ double rinv[MAXK], cmu[MAXK];
     __shared__ int bad, badp;
     const int K2 = 2 * k;
     const int t = threadIdx.x, nt = blockDim.x;
@@ -218,7 +223,10 @@ constexpr int RR_SWEEPS = 40;
 __global__ void __launch_bounds__(SMALL_THREADS)
 k_rayleigh_ritz(const double *__restrict__ G, int k, double *__restrict__ theta,
                 double *__restrict__ W) {
-    __shared__ double sA[MAXK * SLD], sR[MAXK * SLD], sZ[MAXK * SLD], sT[MAXK * SLD], rinv[MAXK];
+    // four k x k work arrays (RR_SMEM bytes of dynamic shared memory)
+    extern __shared__ __align__(16) double rr_smem[];
+    double *sA = rr_smem, *sR = sA + MAXK * SLD, *sZ = sR + MAXK * SLD, *sT = sZ + MAXK * SLD;
+    __shared__ double rinv[MAXK];
     __shared__ double rc[MAXK / 2], rs[MAXK / 2], red[SMALL_THREADS / 32][2];
     __shared__ int bad, perm[MAXK], done;
     const int t = threadIdx.x, nt = blockDim.x;
@@ -384,7 +392,8 @@ static sped_status run_update(int64_t n, void *V, int ldv, const void *Y, int ld
     else if (k <= 16) UPD(16);
     else if (k <= 20) UPD(20);
     else if (k <= 24) UPD(24);
-    else UPD(32);
+    else if (k <= 32) UPD(32);
+    else UPD(40);
 #undef UPD
     return SPED_OK;
 }
@@ -457,7 +466,9 @@ static sped_status eig_step_impl(const sped_graph *g, const sped_step_opts *o, v
     shared.used = 0;
     SPED_TRY(launch_gram(g->n, V, vt, ld, k, Y, o->y_t, L.ldy, k, G, shared, st));
     SPED_CUDA(cudaMemsetAsync(&cf->err, 0, sizeof(int), st));
-    k_small<<<1, SMALL_THREADS, 0, st>>>(G, k, o->eta, (int)o->solver, cf, d_stats);
+    SPED_CUDA(cudaFuncSetAttribute(k_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)SMALL_SMEM));
+    k_small<<<1, SMALL_THREADS, SMALL_SMEM, st>>>(G, k, o->eta, (int)o->solver, cf, d_stats);
     SPED_CHECK_LAUNCH("k_small");
     const int bdiag = o->solver == SPED_SOLVER_MU_EG;  // mu-EG: Y enters through eta I
     __nv_bfloat16 *shadow = (__nv_bfloat16 *)o->v_shadow;
@@ -509,7 +520,7 @@ sped_status sped_eig_step(const sped_graph *g, const sped_step_opts *opts, void 
 }
 
 sped_status sped_rayleigh_scratch_size(const sped_graph *g, int k, size_t *bytes) {
-    if (!g || !bytes || k < 1 || 2 * k > 64) return fail(SPED_ERR_INVALID_ARG, "rayleigh_scratch_size");
+    if (!g || !bytes || k < 1 || k > MAXK) return fail(SPED_ERR_INVALID_ARG, "rayleigh_scratch_size");
     ScratchPlan p;
     p.add((size_t)g->n * padded_ld(k, SPED_F64) * 8);
     p.add(sizeof(double) * 4 * k * k);
@@ -522,7 +533,7 @@ sped_status sped_rayleigh_scratch_size(const sped_graph *g, int k, size_t *bytes
 sped_status sped_rayleigh(const sped_graph *g, const void *d_V, sped_dtype v_t, int k, int ld,
                           double *d_out, void *d_scratch, size_t scratch_bytes, void *stream) {
     if (!g || !d_out) return fail(SPED_ERR_INVALID_ARG, "rayleigh: null");
-    if (k < 1 || 2 * k > 64) return fail(SPED_ERR_UNSUPPORTED, "rayleigh: k=%d", k);
+    if (k < 1 || k > MAXK) return fail(SPED_ERR_UNSUPPORTED, "rayleigh: k=%d (1..%d)", k, MAXK);
     if (v_t != SPED_F32 && v_t != SPED_F64)
         return fail(SPED_ERR_UNSUPPORTED, "rayleigh: V must be F32 or F64");
     SPED_TRY(check_layout(d_V, v_t, k, ld, "rayleigh V"));
@@ -571,7 +582,9 @@ sped_status sped_rayleigh_ritz(const sped_graph *g, void *d_V, sped_dtype v_t, i
     SPED_TRY(launch_poly_step(g, k, d_V, v_t, ld, nullptr, v_t, ld, LV, SPED_F64, ldl, 0.0, 1.0,
                               0.0, 0, scr, st));
     SPED_TRY(launch_gram(g->n, d_V, v_t, ld, k, LV, SPED_F64, ldl, k, G, scr, st));
-    k_rayleigh_ritz<<<1, SMALL_THREADS, 0, st>>>(G, k, d_theta, Wk);
+    SPED_CUDA(cudaFuncSetAttribute(k_rayleigh_ritz, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)RR_SMEM));
+    k_rayleigh_ritz<<<1, SMALL_THREADS, RR_SMEM, st>>>(G, k, d_theta, Wk);
     SPED_CHECK_LAUNCH("k_rayleigh_ritz");
     if (d_W) SPED_CUDA(cudaMemcpyAsync(d_W, Wk, sizeof(double) * k * k, cudaMemcpyDeviceToDevice, st));
     if (rotate)  // V <- V W in place: each row is read whole before it is written

@@ -6,7 +6,7 @@
 
 namespace sped {
 
-constexpr int MAXK = 32;
+constexpr int MAXK = 40;
 
 enum : int { SOLVE_ERR_NOT_PD = 1, SOLVE_ERR_NAN = 2 };
 

@@ -17,7 +17,7 @@ pytestmark = pytest.mark.gpu
                                        (torch.bfloat16, torch.bfloat16, 1e-6),
                                        (torch.float32, torch.float64, 1e-13)])
 @pytest.mark.parametrize("n,ka,kb", [(1, 1, 0), (1000, 4, 4), (33333, 20, 20), (5000, 32, 32),
-                                     (777, 7, 3)])
+                                     (777, 7, 3), (4099, 40, 40), (3001, 37, 36)])
 def test_gram(at, bt, tol, n, ka, kb):
     A0 = gen.gaussian_block(n, ka, seed=1)
     B0 = gen.gaussian_block(n, kb, seed=2) if kb else None
@@ -210,7 +210,7 @@ def test_rayleigh_on_closed_form_eigenvectors():
     assert np.allclose(lam, [2 - 2 * np.cos(np.pi * j / n) for j in js], rtol=1e-12)
 
 
-@pytest.mark.parametrize("k", [1, 5, 8, 13, 32])
+@pytest.mark.parametrize("k", [1, 5, 8, 13, 32, 33, 40])
 @pytest.mark.parametrize("vt", [torch.float64, torch.float32])
 def test_rayleigh_ritz_matches_oracle(k, vt):
     g = gen.sbm(1200, 4, 0.03, 0.002, seed=30 + k)
@@ -310,3 +310,52 @@ def test_solve_reports_a_timed_out_wait():
     finally:
         sped.test_gram_waits(0, False)
     sped.device_status()
+
+
+@pytest.mark.parametrize("solver", [sped.MU_EG, sped.OJA])
+@pytest.mark.parametrize("k", [33, 40])
+def test_eig_step_fp64_wide_blocks(solver, k):
+    # k in (32, 40]: the widest update kernel, the k x k stage in dynamic shared memory and the
+    # 2k-column Gram on the CUDA cores
+    g = gen.sbm(2500, 5, 0.02, 0.001, seed=70 + k)
+    G = sped.Graph.from_csr(g)
+    info = G.set_polynomial(sped.POLY_LIMIT_EXP, 7)
+    V0 = gen.gaussian_block(g.n, k, seed=71)
+    V0 /= np.linalg.norm(V0, axis=0)
+    V = to_block(V0, torch.float64)
+    eta = 0.5 if solver == sped.MU_EG else 2.0
+    opts = sped.step_opts(solver, eta, torch.float64, torch.float64)
+    stats = torch.zeros(3 * k, dtype=torch.float64, device=DEV)
+    sped.eig_step(G, V, k, opts, stats=stats)
+    torch.cuda.synchronize()
+    Y0 = oracle.poly_limit(g, V0, info.scale_s, 7)
+    want = oracle.mu_eg_step(V0, Y0, eta) if solver == sped.MU_EG else oracle.oja_step(V0, Y0, eta)
+    assert_close(host(V, k), want, 1e-10)
+    assert np.allclose(stats.cpu().numpy()[:k], oracle.ritz_values(V0, Y0), rtol=1e-11)
+
+
+def test_mixed_eig_step_k36():
+    g = gen.sbm(6000, 6, 0.01, 0.0004, seed=75)
+    G = sped.Graph.from_csr(g)
+    info = G.set_polynomial(sped.POLY_LIMIT_EXP, 21)
+    k = 36
+    V0 = gen.gaussian_block(g.n, k, seed=76)
+    V0 /= np.linalg.norm(V0, axis=0)
+    V = to_block(V0, torch.float32)
+    Vb = sped.alloc_block(g.n, k, torch.bfloat16, DEV)
+    opts = sped.step_opts(sped.OJA, 0.0, torch.bfloat16, torch.float32, v_shadow=Vb)
+    sped.eig_step(G, V, k, opts)
+    torch.cuda.synchronize()
+    assert torch.equal(Vb[:, :k], V[:, :k].to(torch.bfloat16))
+    Vs = stored(V0, torch.float32)
+    Y = oracle.poly_limit(g, Vs, info.scale_s, 21)
+    orth = lambda Yp: oracle.oja_step(np.zeros_like(Vs), Yp, 1.0)
+    assert_step_close(host(V, k), orth(Y), orth, Y, 1e-2)
+
+
+def test_eig_step_rejects_more_than_40_columns():
+    g = gen.sbm(500, 2, 0.05, 0.01, seed=3)
+    G = sped.Graph.from_csr(g)
+    V = to_block(gen.gaussian_block(g.n, 41, seed=4), torch.float64)
+    with pytest.raises(sped.SpedError):
+        sped.eig_step(G, V, 41, sped.step_opts(sped.OJA, 0.0, torch.float64, torch.float64))
