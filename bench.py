@@ -407,7 +407,7 @@ def pick_graded_k(theta, k_min, rel_gap=0.05):
     return kk, rel[kk - 1]
 
 
-def ttk_benchmark_graph(sped, torch, g, G, dev, stream, k_min, ell, kp=32, probe_steps=30,
+def ttk_benchmark_graph(sped, torch, g, G, dev, stream, k_min, ell, kp=40, probe_steps=40,
                         min_rel_gap=0.02):
     """Time-to-bottom-k on the benchmark SBM itself. Its bottom-20 sits inside a cluster of
     block modes and modes localized at low-degree nodes with no clear gap after the 20th, so the
@@ -415,7 +415,7 @@ def ttk_benchmark_graph(sped, torch, g, G, dev, stream, k_min, ell, kp=32, probe
     vectors on the dilated operator gives the Ritz values, pick_graded_k picks k (leaving four
     guard vectors for the reference), and the mixed-precision dilated arms race the plain-L
     FP64 arms at that k. When no gap of at least min_rel_gap exists below kp - 4 (the solver
-    path takes k <= 32), the probe is reported and nothing is graded."""
+    path takes k <= 40), the probe is reported and nothing is graded."""
     res, _ = spectrum_probe(sped, torch, G, g.n, dev, kp=kp, steps=(probe_steps,))
     theta = res[probe_steps]["ritz"]
     kk, gap = pick_graded_k(theta, k_min)
@@ -426,8 +426,8 @@ def ttk_benchmark_graph(sped, torch, g, G, dev, stream, k_min, ell, kp=32, probe
                        "probe_max_residual": res[probe_steps]["max_residual"],
                        "why": f"no relative Ritz gap >= {min_rel_gap} for k in [{k_min}, "
                               f"{kp - 4}] (largest {gap:.3g} at k = {kk}); the solver path "
-                              f"takes k <= 32"}}
-    r = time_to_bottom_k(sped, torch, g, kk, dev, stream, ell, ref_steps=40, kp=min(kk + 4, 32),
+                              f"takes k <= 40"}}
+    r = time_to_bottom_k(sped, torch, g, kk, dev, stream, ell, ref_steps=40, kp=min(kk + 4, 40),
                          arms=("dilated_mixed_oja", "dilated_mixed_mu_eg", "dilated_fp64_oja",
                                "plain_fp64_oja", "plain_fp64_mu_eg"))
     G.set_polynomial(sped.POLY_LIMIT_EXP, ell)
