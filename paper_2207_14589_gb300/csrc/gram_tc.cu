@@ -281,6 +281,7 @@ k_gram_ws(int64_t n, const Ta *__restrict__ A, int lda, int ka, const Tb *__rest
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
+    pdl_wait();  // the set-up above overlaps the previous kernel; its outputs are read below
     const uint32_t tmem = sm.tmem_base;
     int64_t issued = 0;      // producer (warp 0, lane 0): fills issued
     int64_t mma_issued = 0;  // MMA warp, lane 0: tiles whose MMAs were issued
@@ -531,6 +532,7 @@ k_gram_ws(int64_t n, const Ta *__restrict__ A, int lda, int ka, const Tb *__rest
         out[i * K2 + j] = v;
         out[j * K2 + i] = v;
     }
+    pdl_trigger();
 }
 
 // G[e] = sum over CTAs of partial[c][e]: a block per 32 outputs, 32 thread groups over the
@@ -539,6 +541,7 @@ constexpr int RED_OUT = 32, RED_GROUPS = 32;
 __global__ void __launch_bounds__(RED_OUT *RED_GROUPS)
 k_gram_tc_reduce(const double *__restrict__ partial, int nparts, int K2, double *__restrict__ G) {
     __shared__ double sm[RED_GROUPS][RED_OUT];
+    pdl_wait();
     const int o = threadIdx.x % RED_OUT, grp = threadIdx.x / RED_OUT;
     const int e = blockIdx.x * RED_OUT + o;
     const int tot = K2 * K2;
@@ -565,6 +568,7 @@ k_gram_tc_reduce(const double *__restrict__ partial, int nparts, int K2, double 
         for (int q = 0; q < RED_GROUPS; ++q) r += sm[q][o];
         G[e] = r;
     }
+    pdl_trigger();
 }
 
 static int tc_ctas(int64_t n) {
@@ -606,12 +610,13 @@ static sped_status run_tc(int64_t n, const void *A, int lda, int ka, const void 
     const size_t smem = sizeof(WsSmem) + 1024;
     auto kern = k_gram_ws<Ta, Tb, S>;
     SPED_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<ctas, WS_THREADS, smem, st>>>(n, (const Ta *)A, lda, ka, (const Tb *)B, ldb, kb, partial,
-                                         lim ? lim : TC_WAIT_LIMIT, g_tc_skip_fills.load());
+    SPED_CUDA(launch_pdl(kern, dim3(ctas), dim3(WS_THREADS), smem, st, n, (const Ta *)A, lda, ka,
+                         (const Tb *)B, ldb, kb, partial, lim ? lim : TC_WAIT_LIMIT,
+                         g_tc_skip_fills.load()));
     SPED_CHECK_LAUNCH("k_gram_ws");
     const int K2 = ka + kb;
-    k_gram_tc_reduce<<<(K2 * K2 + RED_OUT - 1) / RED_OUT, RED_OUT * RED_GROUPS, 0, st>>>(
-        partial, ctas, K2, G);
+    SPED_CUDA(launch_pdl(k_gram_tc_reduce, dim3((K2 * K2 + RED_OUT - 1) / RED_OUT),
+                         dim3(RED_OUT * RED_GROUPS), 0, st, (const double *)partial, ctas, K2, G));
     SPED_CHECK_LAUNCH("k_gram_tc_reduce");
     return SPED_OK;
 }

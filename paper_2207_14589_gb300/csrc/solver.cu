@@ -86,6 +86,7 @@ k_small(const double *__restrict__ G, int k, double eta, int solver, Coefs *cf, 
     double *sP = small_smem, *sH = sP + MAXK * SLD, *sW = sH + MAXK * SLD, *sR = sW + MAXK * SLD,
            *sB = sR + MAXK * SLD;
     __shared__ double rinv[MAXK], cmu[MAXK];
+    pdl_wait();  // launched with programmatic dependent launch: G comes from the kernel before
     __shared__ int bad, badp;
     const int K2 = 2 * k;
     const int t = threadIdx.x, nt = blockDim.x;
@@ -468,7 +469,8 @@ static sped_status eig_step_impl(const sped_graph *g, const sped_step_opts *o, v
     SPED_CUDA(cudaMemsetAsync(&cf->err, 0, sizeof(int), st));
     SPED_CUDA(cudaFuncSetAttribute(k_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)SMALL_SMEM));
-    k_small<<<1, SMALL_THREADS, SMALL_SMEM, st>>>(G, k, o->eta, (int)o->solver, cf, d_stats);
+    SPED_CUDA(launch_pdl(k_small, dim3(1), dim3(SMALL_THREADS), SMALL_SMEM, st,
+                         (const double *)G, k, o->eta, (int)o->solver, cf, d_stats));
     SPED_CHECK_LAUNCH("k_small");
     const int bdiag = o->solver == SPED_SOLVER_MU_EG;  // mu-EG: Y enters through eta I
     __nv_bfloat16 *shadow = (__nv_bfloat16 *)o->v_shadow;

@@ -41,6 +41,26 @@ sped_status cuda_fail(cudaError_t e, const char *where);
 
 inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
+// Launch with programmatic dependent launch: the kernel may be scheduled while the previous
+// kernel in the stream is finishing. Every kernel launched this way executes pdl_wait() before
+// its first access to memory another kernel writes, and pdl_trigger() once its own stores are
+// issued.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t st, Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args &&>(args)...);
+}
+
 inline size_t dtype_size(sped_dtype t) {
     return t == SPED_BF16 ? 2 : (t == SPED_F32 ? 4 : 8);
 }
@@ -153,6 +173,13 @@ template <int BYTES> struct VecOf;
 template <> struct VecOf<4> { using type = uint32_t; };
 template <> struct VecOf<8> { using type = uint2; };
 template <> struct VecOf<16> { using type = uint4; };
+
+// programmatic dependent launch: wait for the previous kernel of the stream (its writes
+// visible), and let the next one be scheduled
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
 
 // BF16 -> F32 of the two halves of a 32-bit word: a BF16 value is the top half of the F32 with
 // the same bits, so the conversion is a shift or a mask (exact)

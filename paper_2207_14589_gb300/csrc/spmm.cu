@@ -127,7 +127,7 @@ __device__ __forceinline__ void gather_range(const StepArgs<Tx, Tv, Ty, A, W, HV
 template <typename Tx, typename Tv, typename Ty, typename A, bool W, int HV>
 __global__ void __launch_bounds__(STEP_THREADS)
 k_step_rowgroup(StepArgs<Tx, Tv, Ty, A, W, HV> a, int rows_per_warp) {
-    asm volatile("griddepcontrol.wait;" ::: "memory");
+    pdl_wait();
     constexpr int E = 16 / (int)sizeof(Tx);
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * STEP_THREADS + threadIdx.x) >> 5;
@@ -144,7 +144,7 @@ k_step_rowgroup(StepArgs<Tx, Tv, Ty, A, W, HV> a, int rows_per_warp) {
     gather_range<Tx, Tv, Ty, A, W, HV, E>(a, c, p0, p1, acc, dsum);
     if constexpr (!W) dsum = (A)(p1 - p0);
     finish_row<Tx, Tv, Ty, A, W, HV, E>(a, r, c, acc, dsum);
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    pdl_trigger();
 }
 
 // ---------------------------------------------------------------------------------------
@@ -411,19 +411,9 @@ static sped_status run_step(const sped_graph *g, int k, const void *X, int ldx, 
     if (!use_merge(g, split)) {
         int64_t warps = (g->n + per_warp - 1) / per_warp;
         int64_t blocks = (warps * 32 + STEP_THREADS - 1) / STEP_THREADS;
-        if (blocks > 0) {
-            cudaLaunchConfig_t cfg = {};
-            cfg.gridDim = dim3((unsigned)blocks);
-            cfg.blockDim = dim3(STEP_THREADS);
-            cfg.dynamicSmemBytes = 0;
-            cfg.stream = st;
-            cudaLaunchAttribute attr[1];
-            attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-            attr[0].val.programmaticStreamSerializationAllowed = 1;
-            cfg.attrs = attr;
-            cfg.numAttrs = 1;
-            SPED_CUDA(cudaLaunchKernelEx(&cfg, k_step_rowgroup<Tx, Tv, Ty, A, W, HV>, a, per_warp));
-        }
+        if (blocks > 0)
+            SPED_CUDA(launch_pdl(k_step_rowgroup<Tx, Tv, Ty, A, W, HV>, dim3((unsigned)blocks),
+                                 dim3(STEP_THREADS), 0, st, a, per_warp));
         SPED_CHECK_LAUNCH("k_step_rowgroup");
         return SPED_OK;
     }

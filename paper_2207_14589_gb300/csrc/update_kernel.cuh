@@ -48,6 +48,7 @@ k_update(int64_t n, Tm *__restrict__ V, int ldv, const Ty *__restrict__ Y, int l
     __shared__ __align__(16) A sC[STATS ? KM * KM : 4];
     __shared__ A sS[KM];
     __shared__ double sdv[KM], sres[KM];
+    pdl_wait();  // launched with programmatic dependent launch: the coefficients, V and Y
     for (int e = threadIdx.x; e < KM * KM; e += blockDim.x) {
         const int j = e / KM, i = e % KM;
         const bool in = i < k && j < k;
@@ -169,6 +170,7 @@ k_update(int64_t n, Tm *__restrict__ V, int ldv, const Ty *__restrict__ Y, int l
             atomicAdd(&cf->res2[threadIdx.x], sres[threadIdx.x]);
         }
     }
+    pdl_trigger();
 }
 
 template <typename Tm, typename Ty, int KM>
@@ -176,11 +178,11 @@ sped_status launch_update(int blocks, int64_t n, void *V, int ldv, const void *Y
                           Coefs *cf, int bdiag, int vec, bool stats, __nv_bfloat16 *shadow,
                           int lds, cudaStream_t st) {
     if (stats)
-        k_update<Tm, Ty, KM, true><<<blocks, 256, 0, st>>>(n, (Tm *)V, ldv, (const Ty *)Y, ldy, k,
-                                                          cf, bdiag, vec, shadow, lds);
+        SPED_CUDA(launch_pdl(k_update<Tm, Ty, KM, true>, dim3(blocks), dim3(256), 0, st, n,
+                             (Tm *)V, ldv, (const Ty *)Y, ldy, k, cf, bdiag, vec, shadow, lds));
     else
-        k_update<Tm, Ty, KM, false><<<blocks, 256, 0, st>>>(n, (Tm *)V, ldv, (const Ty *)Y, ldy,
-                                                           k, cf, bdiag, vec, shadow, lds);
+        SPED_CUDA(launch_pdl(k_update<Tm, Ty, KM, false>, dim3(blocks), dim3(256), 0, st, n,
+                             (Tm *)V, ldv, (const Ty *)Y, ldy, k, cf, bdiag, vec, shadow, lds));
     SPED_CHECK_LAUNCH("k_update");
     return SPED_OK;
 }
