@@ -85,3 +85,31 @@ def test_batched_full_workload_sampled_graphs():
         want = oracle.mu_eg_step(Vi, Yi, eta)
         got = V[off[i]:off[i + 1], :k].double().cpu().numpy()
         assert_step_close(got, want, lambda Yp: oracle.mu_eg_step(Vi, Yp, eta), Yi, 1e-2, seed=i)
+
+
+@pytest.mark.parametrize("dt,tol_v,tol_w", [(torch.float64, 1e-10, 1e-9),
+                                            (torch.float32, 1e-4, 1e-4)])
+def test_differentiable_full_size(dt, tol_v, tol_w):
+    # the differentiable workload at its full size: SBM N = 200,000, 10 blocks, mean degree 20,
+    # 87.5 % intra-block edge ends, weights U(0.5, 1.5), k = 10, degree 11; the gradients of
+    # sum_i g_i u_i w.r.t. V (adjoint chain) and w.r.t. every edge weight (checkpointed SDDMM)
+    # against the oracle's analytic gradients
+    g = gen.uniform_edge_weights(gen.sbm_by_degree(200_000, 10, 20.0, 0.875, seed=5), seed=6)
+    G = sped.Graph.from_csr(g)
+    ell, k = 11, 10
+    info = G.set_polynomial(sped.POLY_LIMIT_EXP, ell)
+    a, b, w = oracle.edge_list(g)
+    V0 = gen.gaussian_block(g.n, k, seed=19)
+    V = to_block(V0, dt).requires_grad_(True)
+    wt = torch.tensor(w, dtype=dt, device=DEV, requires_grad=True)
+    gu = torch.linspace(1.0, 0.1, k, dtype=torch.float64, device=DEV)
+    u = sped.eigengame_utilities(V, wt, G, k)
+    (u * gu).sum().backward()
+    Vs = stored(V0, dt)
+    Y0 = oracle.poly_limit(g, Vs, info.scale_s, ell)
+    gn = gu.cpu().numpy()
+    assert np.allclose(u.detach().cpu().numpy(), oracle.eg_utilities(Vs, Y0), rtol=tol_v)
+    assert_close(V.grad[:, :k].double().cpu().numpy(), oracle.eg_grad_full(Vs, Y0, gn), tol_v)
+    Hb = oracle.eg_utility_hbar(Vs.T @ Y0, gn)
+    assert_close(wt.grad.double().cpu().numpy(),
+                 oracle.limit_edge_grad(g, Vs, info.scale_s, ell, Hb), tol_w)
