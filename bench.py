@@ -195,23 +195,29 @@ def _principal_angle(sped, Vstar, V, k):
 
 
 def certify_reference(g, Vs, k):
-    """Davis-Kahan certificate of a reference subspace, computed by the FP64 oracle on the host
-    (Section 8 of the design: the reference of time-to-bottom-k must not rest on the GPU path
-    alone). Rayleigh-Ritz of L on span(Vs) (kp >= k + 1 columns) gives Ritz pairs
-    (theta_i, u_i); the residual block R = L U_k - U_k Theta_k of the first k Ritz vectors and
-    the gap delta = theta_{k+1} - theta_k to the first guard Ritz value bound the largest
-    principal angle between span(U_k) and the bottom-k eigenvectors of L by
-    sin(theta_max) <= ||R||_2 / delta (sin-theta theorem; delta stands in for
-    lambda_{k+1} - theta_k, as the guard vectors estimate lambda_{k+1}). The reference the
-    arms are graded against is thereby checked by code that shares nothing with the GPU."""
-    import oracle
-    Vh = np.ascontiguousarray(Vs, dtype=np.float64)
-    theta, W = oracle.rayleigh_ritz(g, Vh)
-    U = Vh @ W[:, :k]
-    R = oracle.laplacian_apply(g, U) - U * theta[:k]
+    """Davis-Kahan certificate of a reference subspace, computed on the host in FP64 with
+    scipy.sparse (the Laplacian written out from the CSR arrays) and numpy, so that the reference
+    the arms are graded against does not rest on the GPU path alone. Rayleigh-Ritz of L on
+    span(Vs) (kp >= k + 1 columns, orthonormalised by QR) gives Ritz pairs (theta_i, u_i); the
+    residual block R = L U_k - U_k Theta_k of the first k Ritz vectors and the gap
+    delta = theta_{k+1} - theta_k to the first guard Ritz value bound the largest principal
+    angle between span(U_k) and the bottom-k eigenvectors of L by sin(theta_max) <= ||R||_2 /
+    delta (sin-theta theorem; delta stands in for lambda_{k+1} - theta_k, as the guard vectors
+    estimate lambda_{k+1})."""
+    import scipy.sparse as sp
+    n = g.n
+    w = np.ones(g.nnz) if g.w is None else g.w.astype(np.float64)
+    A = sp.csr_matrix((w, g.col_idx.astype(np.int64), g.row_ptr.astype(np.int64)), shape=(n, n))
+    L = sp.diags(np.asarray(A.sum(axis=1)).ravel()) - A
+    Q, _ = np.linalg.qr(np.ascontiguousarray(Vs, dtype=np.float64))
+    H = Q.T @ (L @ Q)
+    theta, Z = np.linalg.eigh(0.5 * (H + H.T))
+    U = Q @ Z[:, :k]
+    R = L @ U - U * theta[:k]
     rnorm = float(math.sqrt(max(0.0, np.linalg.eigvalsh(R.T @ R).max())))
     gap = float(theta[k] - theta[k - 1])
-    return {"by": "oracle (FP64 CPU Rayleigh-Ritz and residual of the GPU reference block)",
+    return {"by": "host FP64 (scipy.sparse Laplacian, numpy Rayleigh-Ritz and residual of the "
+                  "GPU reference block)",
             "ritz_values": [float(x) for x in theta[:k + 1]],
             "residual_2norm": rnorm, "gap_theta_k1_minus_theta_k": gap,
             "davis_kahan_sin_theta_bound": rnorm / gap if gap > 0 else None}

@@ -2,6 +2,8 @@
 solver step, written out term by term for the benchmark workload."""
 import json
 
+import pytest
+
 import bench
 
 
@@ -85,3 +87,25 @@ def test_graded_k_picks_the_nearest_clear_gap():
     theta = [0.0, 0.9] + [1.8 + 0.001 * i for i in range(30)] + [2.7, 2.8, 2.9, 3.0, 3.1]
     k, gap = bench.pick_graded_k(theta, 20)
     assert k == 32 and gap > 0.3
+
+
+def test_reference_certificate_matches_the_oracle():
+    # the time-to-bottom-k certificate is host FP64 code of the benchmark's own (scipy.sparse
+    # Laplacian, numpy Rayleigh-Ritz); its Ritz values and residual bound must agree with the
+    # oracle's Rayleigh-Ritz and residual on a weighted graph and a perturbed bottom subspace
+    import numpy as np
+    import gen
+    import oracle
+    g = gen.uniform_edge_weights(gen.sbm(400, 4, 0.1, 0.005, seed=3), seed=4)
+    lam, U = np.linalg.eigh(oracle.dense_laplacian(g))
+    k, kp = 4, 8
+    V = U[:, :kp] + 1e-6 * np.random.default_rng(0).standard_normal((g.n, kp))
+    c = bench.certify_reference(g, V, k)
+    theta, W = oracle.rayleigh_ritz(g, V)
+    assert np.allclose(c["ritz_values"], theta[:k + 1], rtol=1e-10, atol=1e-12)
+    Uk = V @ W[:, :k]
+    R = oracle.laplacian_apply(g, Uk) - Uk * theta[:k]
+    assert c["residual_2norm"] == pytest.approx(np.linalg.norm(R, 2), rel=1e-8)
+    # the bound holds against the dense eigendecomposition
+    ang = oracle.principal_angle_max(U[:, :k], Uk)
+    assert np.sin(ang) <= c["davis_kahan_sin_theta_bound"] * (1 + 1e-9)
