@@ -800,6 +800,73 @@ def measure_three_room(sped, torch, dev, stream, k=3, cap_plain=20000, cap_dilat
     return out
 
 
+def _streak_device(torch, Ud, V, k, eps):
+    """Section 5.2's eigenvector streak on the device: the length of the leading run of columns
+    of V whose angle to the matching column of Ud (unit eigenvectors) is at most eps, sign
+    ignored; also returns the per-column angles."""
+    X = V[:, :k]
+    X = X / X.norm(dim=0, keepdim=True)
+    U = Ud[:, :k]
+    c = (X * U).sum(dim=0, keepdim=True)
+    ang = torch.asin(torch.clamp((X - c * U).norm(dim=0), max=1.0)).cpu().numpy()
+    n = 0
+    for a in ang:
+        if a > eps:
+            break
+        n += 1
+    return n, [float(a) for a in ang]
+
+
+def measure_link_prediction(sped, torch, dev, stream, k=4, cap_plain=5000, cap_dilated=2000):
+    """App. A.1 (clustering probabilistic graphs): four 250-cliques joined by 25 short-circuit
+    edges (n = 1,000), each edge removed with probability 0.2 and put back with its
+    common-neighbours score over the largest score as weight. Oja (eta = 0) and mu-EG in FP64,
+    plain reversed Laplacian against the limit form of degree 251: steps until the eigenvector
+    streak (Section 5.2, eps = pi/8) covers all k bottom eigenvectors, and the streak after 10,
+    100 and 1,000 steps (the paper plots the streak over training)."""
+    g, removed = gen.link_completed_cliques([250] * 4, short_circuit=25, p_remove=0.2, seed=SEED)
+    n = g.n
+    Ld = np.zeros((n, n))
+    rows = np.repeat(np.arange(n), np.diff(g.row_ptr))
+    Ld[rows, g.col_idx] = -g.w
+    Ld[np.arange(n), np.arange(n)] = -Ld.sum(axis=1)
+    lam, U = np.linalg.eigh(Ld)
+    Ud = torch.from_numpy(U[:, :k]).to(dev)
+    G = sped.Graph.from_csr(g, device=dev)
+    V0 = torch.from_numpy(gen.gaussian_block(n, k, seed=SEED + 31)).to(dev)
+    eps = math.pi / 8
+    out = {"graph": g.name, "n": n, "nnz": g.nnz, "k": k, "removed_edges": int(removed.shape[1]),
+           "predicted_edges_kept": int((g.w < 1).sum() // 2),
+           "lambda": [float(x) for x in lam[:k + 1]], "eps": eps}
+    arms = {"plain_oja": ("shift", sped.OJA, 0.0, cap_plain),
+            "dilated251_oja": ("limit", sped.OJA, 0.0, cap_dilated),
+            "plain_mu_eg": ("shift", sped.MU_EG, None, cap_plain),
+            "dilated251_mu_eg": ("limit", sped.MU_EG, 1.0, cap_dilated)}
+    for name, (poly, solver, eta, cap) in arms.items():
+        info = (G.set_polynomial(sped.POLY_LIMIT_EXP, 251) if poly == "limit"
+                else G.set_polynomial(sped.POLY_SHIFT, 1))
+        e = eta if eta is not None else 2.0 / info.lambda_star
+        opts = sped.step_opts(solver, e, torch.float64, torch.float64)
+        V = sped.alloc_block(n, k, torch.float64, dev)
+        V[:, :k] = V0
+        scr = torch.empty(sped.eig_step_scratch_bytes(G, opts, k), dtype=torch.uint8, device=dev)
+        steps, at = None, {}
+        streak, ang = 0, None
+        for t in range(1, cap + 1):
+            sped.eig_step(G, V, k, opts, scratch=scr)
+            if t in (10, 100, 1000) or poly == "limit" or t % 10 == 0 or t == cap:
+                streak, ang = _streak_device(torch, Ud, V, k, eps)
+                if t in (10, 100, 1000):
+                    at[f"streak_at_{t}"] = streak
+                if streak == k:
+                    steps = t
+                    break
+        out[name] = {"steps_to_full_streak": steps,
+                     "spmm": None if steps is None else steps * info.degree,
+                     "final_streak": streak, "final_angles": ang, "eta": e, **at}
+    return out
+
+
 def _cheb_quadratic_forms(mu, d, k, a, b):
     """From the block moments mu_l = V^T T_l V (l <= 2d + 1) of the Chebyshev basis on [a, b]:
     A[l, m] = V^T T_l T_m V = (mu_{l+m} + mu_{|l-m|}) / 2 and Bm[l, m] = V^T T_l L T_m V, with
@@ -1231,6 +1298,7 @@ def run_ours(args, rank, world, local_rank):
             "permuted_node_order": lambda: measure_permuted(sped, torch, dev, stream, k, ell),
             "degree_sweep": lambda: measure_degree_sweep(sped, torch, dev, stream),
             "three_room": lambda: measure_three_room(sped, torch, dev, stream),
+            "link_prediction": lambda: measure_link_prediction(sped, torch, dev, stream),
             "fitted_poly": lambda: measure_fitted_poly(sped, torch, dev, stream)}
         # gathered bytes of one chain step (every stored entry pulls one k-column row)
         extra["gather_bytes_per_launch"] = g.nnz * k * 2
@@ -1374,7 +1442,7 @@ def main():
     ap.add_argument("--only-extra", default=None,
                     help="comma list of the extra measurements to run (stochastic, minibatch, "
                          "differentiable, batched, permuted_node_order, degree_sweep, "
-                         "three_room, fitted_poly); default all")
+                         "three_room, link_prediction, fitted_poly); default all")
     ap.add_argument("--batched-graphs", type=int, default=4096,
                     help="number of graphs of the batched measurement")
     ap.add_argument("--no-power-law", action="store_true",

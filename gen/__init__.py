@@ -10,7 +10,8 @@ Graph conventions (shared by every consumer):
   * a weighted graph carries one weight per undirected edge, written to both directions.
 
 Workload families follow the paper's experiments (all synthetic in the paper too): stochastic
-block models and planted clusters (Section 5.4, Appendix A.1), the 3-room grid world
+block models and planted clusters (Section 5.4), cliques completed by link prediction
+(Appendix A.1), the 3-room grid world
 (Section 5.3), and closed-form graphs used to pin the oracle (path, cycle, complete, star,
 grid, disjoint cliques; Section 2).
 """
@@ -25,6 +26,7 @@ __all__ = [
     "CSRGraph", "from_edges", "path", "cycle", "complete", "star", "grid", "cliques",
     "sbm", "sbm_regular", "sbm_by_degree", "chung_lu_clusters", "batched_sbm", "concat_graphs",
     "random_graph", "three_room_grid", "gaussian_block", "uniform_edge_weights",
+    "common_neighbour_scores", "link_completed_cliques",
     "undirected_edges", "DEFAULT_SEED",
 ]
 
@@ -206,6 +208,46 @@ def cliques(sizes, short_circuit: int = 0, seed: int = DEFAULT_SEED) -> CSRGraph
         b_list += eb
     return from_edges(n, np.concatenate(a_list), np.concatenate(b_list), labels=labels,
                       name=f"cliques{sizes}")
+
+
+def common_neighbour_scores(n: int, oa, ob, ra, rb) -> np.ndarray:
+    """Common-neighbours link prediction: for each candidate pair (ra[i], rb[i]) the number of
+    neighbours its two ends share in the observed graph with undirected edges (oa, ob). Dense
+    n x n adjacency: small graphs only."""
+    if n > 8192:
+        raise ValueError("common_neighbour_scores: n above 8192")
+    adj = np.zeros((n, n), dtype=np.float32)
+    adj[oa, ob] = 1.0
+    adj[ob, oa] = 1.0
+    cn = np.zeros(len(ra), dtype=np.float32)
+    for s in range(0, len(ra), 4096):
+        cn[s:s + 4096] = np.einsum("ij,ij->i", adj[ra[s:s + 4096]], adj[rb[s:s + 4096]])
+    return cn
+
+
+def link_completed_cliques(sizes, short_circuit: int = 25, p_remove: float = 0.2,
+                           seed: int = DEFAULT_SEED):
+    """App. A.1 workload (clustering probabilistic graphs): a cliques graph of Section 5.4 whose
+    edges are each removed with probability ``p_remove``; every removed edge is scored by
+    common-neighbours link prediction on the observed graph and put back with its score divided
+    by the largest score among the removed edges, so predicted edges carry weights in (0, 1] and
+    observed edges weight 1. A removed edge whose ends share no neighbour scores 0 and stays
+    out. Returns (graph, removed): removed is the 2 x m array of the removed pairs (i < j)."""
+    base = cliques(sizes, short_circuit, seed)
+    n = base.n
+    rng = np.random.default_rng([seed, 1])
+    rows = np.repeat(np.arange(n, dtype=np.int64), np.diff(base.row_ptr))
+    upper = base.col_idx > rows
+    a, b = rows[upper], base.col_idx[upper].astype(np.int64)
+    drop = rng.random(len(a)) < p_remove
+    oa, ob, ra, rb = a[~drop], b[~drop], a[drop], b[drop]
+    cn = common_neighbour_scores(n, oa, ob, ra, rb)
+    keep = cn > 0
+    top = cn.max() if keep.any() else 1.0
+    w = np.concatenate([np.ones(len(oa), dtype=np.float32), cn[keep] / top])
+    g = from_edges(n, np.concatenate([oa, ra[keep]]), np.concatenate([ob, rb[keep]]), w=w,
+                   labels=base.labels, name=f"link_completed_cliques{list(sizes)}")
+    return g, np.stack([ra, rb])
 
 
 # ----------------------------------------------------------------------------------------

@@ -113,3 +113,74 @@ def test_cliques_degree_threshold_pattern(cliques_sc25, ell):
                                          oracle.poly_limit(g, V0, s, ell), 1.0), 1e-10)
     else:
         assert a_gpu > 0.5  # the clique modes took over: far from the bottom-k subspace
+
+
+@pytest.fixture(scope="module")
+def link_completed():
+    # App. A.1: four 100-cliques joined by 25 short-circuit edges, 20 % of the edges removed and
+    # put back with common-neighbours scores as weights in (0, 1]
+    g, _ = gen.link_completed_cliques([100] * 4, short_circuit=25, p_remove=0.2,
+                                      seed=gen.DEFAULT_SEED)
+    lam, U = np.linalg.eigh(oracle.dense_laplacian(g))
+    return g, lam, U
+
+
+def _gpu_oja_run(G, V0, k, steps):
+    """FP64 Oja steps on the GPU; returns the host copy of V after every step."""
+    opts = sped.step_opts(sped.OJA, 0.0, torch.float64, torch.float64)
+    V = to_block(V0, torch.float64)
+    scr = torch.empty(sped.eig_step_scratch_bytes(G, opts, k), dtype=torch.uint8, device=DEV)
+    out = []
+    for _ in range(steps):
+        sped.eig_step(G, V, k, opts, scratch=scr)
+        out.append(host(V, k))
+    return out
+
+
+def test_link_completed_cliques_streak_matches_oracle(link_completed):
+    # the dilated operator (limit form, degree 251) resolves the individual bottom-4
+    # eigenvectors of the weighted, link-completed graph: the GPU's FP64 Oja reaches a streak
+    # of 4 (Section 5.2: every vector within pi/8 of its eigenvector) within one step of the
+    # oracle's iteration from the same V0, and its first step agrees entry by entry
+    g, lam, U = link_completed
+    k = 4
+    assert lam[k] - lam[k - 1] > 50 and lam[k - 1] < 1  # four slow modes, then the cliques
+    G = sped.Graph.from_csr(g)
+    info = G.set_polynomial(sped.POLY_LIMIT_EXP, 251)
+    s = info.scale_s
+    assert s == pytest.approx(oracle.scale_rule(oracle.gershgorin_bound(g), 251))
+    V0 = gen.gaussian_block(g.n, k, seed=31)
+    cap = 160
+    gpu = _gpu_oja_run(G, V0, k, cap)
+    t_gpu = next((t + 1 for t, V in enumerate(gpu)
+                  if oracle.eigenvector_streak(V, U[:, :k], np.pi / 8) == k), None)
+    V, t_orc = V0.copy(), None
+    for t in range(1, cap + 1):
+        V = oracle.oja_step(np.zeros_like(V), oracle.poly_limit(g, V, s, 251), 1.0)
+        if t == 1:
+            assert_close(gpu[0], V, 1e-10)
+        if oracle.eigenvector_streak(V, U[:, :k], np.pi / 8) == k:
+            t_orc = t
+            break
+    assert t_gpu is not None and t_orc is not None, (t_gpu, t_orc)
+    assert abs(t_gpu - t_orc) <= 1, (t_gpu, t_orc)
+
+
+def test_link_completed_cliques_plain_operator_leaves_them_unresolved(link_completed):
+    # the plain reversed Laplacian lambda* I - L separates the four bottom eigenvalues (0 to
+    # 0.15 against lambda* near 200) by factors within 1e-3 of 1 per step: after 300 steps the
+    # streak is still 0, on the GPU as in the oracle's iteration, and the two iterations agree
+    # entry by entry
+    g, lam, U = link_completed
+    k = 4
+    G = sped.Graph.from_csr(g)
+    ls = G.set_polynomial(sped.POLY_SHIFT, 1).lambda_star
+    V0 = gen.gaussian_block(g.n, k, seed=31)
+    steps = 300
+    Vg = _gpu_oja_run(G, V0, k, steps)[-1]
+    V = V0.copy()
+    for _ in range(steps):
+        V = oracle.oja_step(np.zeros_like(V), ls * V - oracle.laplacian_apply(g, V), 1.0)
+    assert oracle.eigenvector_streak(V, U[:, :k], np.pi / 8) == 0
+    assert oracle.eigenvector_streak(Vg, U[:, :k], np.pi / 8) == 0
+    assert_close(Vg, V, 1e-8)
