@@ -716,7 +716,8 @@ def measure_degree_sweep(sped, torch, dev, stream, k=4, cap=200,
     dominant eigenvectors are no longer the bottom of L; at l = 251 it stays below 1. The
     automatic scale (s = 2 / lambda_bound when l < lambda_bound / 2) keeps every degree
     correct. Oja (subspace iteration, eta = 0) in FP64, steps to a largest principal angle
-    <= 1e-3 against the dense eigendecomposition."""
+    <= 1e-3 against the dense eigendecomposition. The Taylor series of -e^{-L} and of
+    log(L + eps) run at the same degrees (App. A.3 compares the series families)."""
     g = gen.cliques([450] * 4, short_circuit=25, seed=SEED)
     n = g.n
     Ld = np.zeros((n, n))
@@ -748,6 +749,27 @@ def measure_degree_sweep(sped, torch, dev, stream, k=4, cap=200,
             out[f"l{deg}_{rule}"] = {"scale_s": info.scale_s, "converged": steps is not None,
                                      "steps": steps, "spmm": None if steps is None else steps * deg,
                                      "final_angle": ang}
+    # App. A.3: the other series of Table 2 at the same degrees (Taylor -e^{-L} with l + 1 terms,
+    # Taylor log(L + eps) around 1), Oja from the same V0
+    for deg in degrees:
+        for fam, kind in (("taylor_exp", sped.POLY_TAYLOR_EXP), ("taylor_log", sped.POLY_TAYLOR_LOG)):
+            G.set_polynomial(kind, deg)
+            V = sped.alloc_block(n, k, torch.float64, dev)
+            V[:, :k] = V0
+            scr = torch.empty(sped.eig_step_scratch_bytes(G, opts, k), dtype=torch.uint8,
+                              device=dev)
+            steps, ang, finite = None, None, True
+            for t in range(1, cap + 1):
+                sped.eig_step(G, V, k, opts, scratch=scr)
+                if not bool(torch.isfinite(V[:, :k]).all()):
+                    finite = False  # the series' values overflowed FP64 (|p(lambda)| > 1e308)
+                    break
+                ang = _principal_angle(sped, Ud, V, k)
+                if ang <= 1e-3:
+                    steps = t
+                    break
+            out[f"l{deg}_{fam}"] = {"converged": steps is not None, "steps": steps,
+                                    "final_angle": ang, "finite": finite, "last_step": t}
     return out
 
 
