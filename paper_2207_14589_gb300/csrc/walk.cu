@@ -19,6 +19,7 @@
 // uniform of prefix i is (word + 0.5) 2^-32 of the first word of tag 0x80000000 | i.
 // Edge ids follow the CSR order of the upper entries (a < b); the step rule takes a's r-th
 // neighbour for r < deg(a), else b's (r - deg(a))-th neighbour with a skipped.
+#include <algorithm>
 #include <cmath>
 
 #include "sped_internal.cuh"
@@ -27,6 +28,13 @@ namespace sped {
 
 constexpr int WALK_MAX_ELL = 511;
 constexpr int WALK_THREADS = 128;
+// Resident blocks per SM the register budget is cut for, from the walker's accumulator size
+// (k columns of the output's precision): 7 blocks (72 registers a thread) while it takes at most
+// 96 bytes, fewer for wider or FP64 accumulators, which would spill under that budget. The walk
+// is bound by the latency of its dependent loads, so resident warps are what it runs on.
+template <typename A, int KM> constexpr int walk_blocks_per_sm() {
+    return (int)sizeof(A) * KM <= 96 ? 7 : ((int)sizeof(A) * KM <= 160 ? 5 : 3);
+}
 
 struct WalkCoefs {
     double c[WALK_MAX_ELL + 1];
@@ -42,22 +50,31 @@ __global__ void k_walk_init(int64_t n, int k, const Tv *__restrict__ V, int ldv,
     Y[r * ldy + j] = from_acc<Ty>(c0 * cvt<double>(V[r * ldv + j]));
 }
 
-// One row of V into registers (the k used columns; 16-byte loads when the layout allows it).
+// scale * (V[a] - V[b]) added into the walker's accumulator one 16-byte chunk of each row at a
+// time (when the layout allows 16-byte loads), so that only a chunk of each row is live instead
+// of two whole rows: the registers saved buy resident warps, which hide the walk's dependent
+// loads. Columns at or past k are not touched (their accumulator entries are never read).
 template <int KM, typename Tv, typename A>
-__device__ __forceinline__ void walk_row(const Tv *p, int k, bool vec, A *out) {
+__device__ __forceinline__ void walk_add(const Tv *pa, const Tv *pb, int k, bool vec, A sc,
+                                         A *acc) {
     constexpr int E = 16 / (int)sizeof(Tv);
     if (vec && KM % E == 0) {
 #pragma unroll
         for (int q = 0; q < KM / E; ++q) {
-            uint4 c = make_uint4(0, 0, 0, 0);
-            if (q * E < k) c = __ldg(reinterpret_cast<const uint4 *>(p) + q);
-            const Tv *e = reinterpret_cast<const Tv *>(&c);
+            if (q * E < k) {
+                const uint4 ca = __ldg(reinterpret_cast<const uint4 *>(pa) + q);
+                const uint4 cb = __ldg(reinterpret_cast<const uint4 *>(pb) + q);
+                const Tv *ea = reinterpret_cast<const Tv *>(&ca);
+                const Tv *eb = reinterpret_cast<const Tv *>(&cb);
 #pragma unroll
-            for (int u = 0; u < E; ++u) out[q * E + u] = cvt<A>(e[u]);
+                for (int u = 0; u < E; ++u)
+                    acc[q * E + u] += sc * (cvt<A>(ea[u]) - cvt<A>(eb[u]));
+            }
         }
     } else {
 #pragma unroll
-        for (int j = 0; j < KM; ++j) out[j] = j < k ? cvt<A>(__ldg(p + j)) : A(0);
+        for (int j = 0; j < KM; ++j)
+            if (j < k) acc[j] += sc * (cvt<A>(__ldg(pa + j)) - cvt<A>(__ldg(pb + j)));
     }
 }
 
@@ -66,7 +83,8 @@ __device__ __forceinline__ void walk_row(const Tv *p, int k, bool vec, A *out) {
 // scale_i (V[a_i] - V[b_i]) runs in the output's precision (F32 output: F32 products of the
 // F32 difference with the FP64 scale rounded once per term).
 template <typename Tv, typename Ty, bool W, int KM, int MODE>
-__global__ void __launch_bounds__(WALK_THREADS)
+__global__ void __launch_bounds__(WALK_THREADS,
+                                  (walk_blocks_per_sm<typename AccOf<Ty>::type, KM>()))
 k_walk(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const float *__restrict__ w,
        const int32_t *__restrict__ rev, const int32_t *__restrict__ edge_p,
        const int32_t *__restrict__ edge_a, int64_t n_edges, const Tv *__restrict__ V, int ldv,
@@ -98,14 +116,9 @@ k_walk(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const flo
                 scale = (u < accept) ? cf.c[i] * alpha * inv_pmin * sw1 * swc : 0.0;
                 inv_pmin *= dstar_inc;
             }
-            if (scale != 0.0) {
-                A va[KM], vb[KM];
-                walk_row<KM>(V + (int64_t)a * ldv, k, vec != 0, va);
-                walk_row<KM>(V + (int64_t)b * ldv, k, vec != 0, vb);
-                const A sc = (A)scale;
-#pragma unroll
-                for (int j = 0; j < KM; ++j) acc[j] += sc * (va[j] - vb[j]);
-            }
+            if (scale != 0.0)
+                walk_add<KM>(V + (int64_t)a * ldv, V + (int64_t)b * ldv, k, vec != 0, (A)scale,
+                             acc);
             if (i == ell) break;
             const int ra = __ldg(rp + a), da = __ldg(rp + a + 1) - ra;
             const int rb = __ldg(rp + b), db = __ldg(rp + b + 1) - rb;
@@ -167,11 +180,12 @@ static sped_status run_walk(const sped_graph *g, int k, const void *V, int ldv, 
     for (int i = 0; i <= WALK_MAX_ELL; ++i) cf.c[i] = i <= ell ? P.power[i] : 0.0;
     double dstar_inc = 2.0 * g->max_deg - 1.0;
     const int vec = ((uintptr_t)V % 16 == 0) && ((size_t)ldv * (sizeof(Tv)) % 16 == 0);
-    int64_t blocks = (walkers + WALK_THREADS - 1) / WALK_THREADS;
-    int64_t cap = (int64_t)device_sm_count() * 16;
-    if (blocks > cap) blocks = cap;
+    // one wave: as many blocks as are resident at once, the grid-stride loop spreads the walkers
+    const int64_t want = (walkers + WALK_THREADS - 1) / WALK_THREADS;
+    using Acc = typename AccOf<Ty>::type;
 #define WALK3(KMV, WV, MV)                                                                     \
-    k_walk<Tv, Ty, WV, KMV, MV><<<(unsigned)blocks, WALK_THREADS, 0, st>>>(                    \
+    k_walk<Tv, Ty, WV, KMV, MV><<<(unsigned)std::min<int64_t>(                                 \
+        want, (int64_t)device_sm_count() * walk_blocks_per_sm<Acc, KMV>()), WALK_THREADS, 0, st>>>( \
         g->rp, g->ci, g->w, g->rev, g->edge_p, g->edge_a, g->n_edges, (const Tv *)V, ldv, k, ell, \
         walkers, seed, dstar_inc, vec, cf, (Ty *)Y, ldy)
 #define WALK(KMV)                                                                              \
