@@ -85,25 +85,40 @@ k_combine(int64_t n, int k, const T *__restrict__ A, int lda, const double *__re
 }
 
 // grad[e] += scale * (A[a] - A[b]) . (C[a] - C[b]) for every undirected edge e = (a, b); the
-// k-term dot in the blocks' precision, the accumulation into grad in FP64
+// k-term dot in the blocks' precision (terms added in column order), the accumulation into grad
+// in FP64. The four rows arrive as 16-byte chunks (the blocks' rows are padded to 16 bytes), so
+// an edge costs 4 ceil(k / E) loads rather than 4 k scalar ones.
 template <typename T, int KM>
 __global__ void __launch_bounds__(256)
 k_sddmm(int64_t n_edges, const int32_t *__restrict__ edge_a, const int32_t *__restrict__ edge_p,
         const int32_t *__restrict__ ci, int k, const T *__restrict__ A, const T *__restrict__ C,
         int ld, double scale, double *__restrict__ grad) {
     using Acc = typename AccOf<T>::type;
+    constexpr int E = 16 / (int)sizeof(T);
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n_edges) return;
     const int a = __ldg(edge_a + e), b = __ldg(ci + __ldg(edge_p + e));
-    const T *Aa = A + (int64_t)a * ld, *Ab = A + (int64_t)b * ld;
-    const T *Ca = C + (int64_t)a * ld, *Cb = C + (int64_t)b * ld;
+    const uint4 *Aa = reinterpret_cast<const uint4 *>(A + (int64_t)a * ld);
+    const uint4 *Ab = reinterpret_cast<const uint4 *>(A + (int64_t)b * ld);
+    const uint4 *Ca = reinterpret_cast<const uint4 *>(C + (int64_t)a * ld);
+    const uint4 *Cb = reinterpret_cast<const uint4 *>(C + (int64_t)b * ld);
     Acc s = Acc(0);
 #pragma unroll
-    for (int i = 0; i < KM; ++i) {
-        if (i < k) {
-            const Acc da = cvt<Acc>(__ldg(Aa + i)) - cvt<Acc>(__ldg(Ab + i));
-            const Acc dc = cvt<Acc>(__ldg(Ca + i)) - cvt<Acc>(__ldg(Cb + i));
-            s += da * dc;
+    for (int q = 0; q < KM / E; ++q) {
+        if (q * E < k) {
+            union { uint4 v; T x[E]; } aa, ab, ca, cb;
+            aa.v = __ldg(Aa + q);
+            ab.v = __ldg(Ab + q);
+            ca.v = __ldg(Ca + q);
+            cb.v = __ldg(Cb + q);
+#pragma unroll
+            for (int u = 0; u < E; ++u) {
+                if (q * E + u < k) {
+                    const Acc da = cvt<Acc>(aa.x[u]) - cvt<Acc>(ab.x[u]);
+                    const Acc dc = cvt<Acc>(ca.x[u]) - cvt<Acc>(cb.x[u]);
+                    s += da * dc;
+                }
+            }
         }
     }
     grad[e] += scale * (double)s;
