@@ -158,6 +158,21 @@ struct SetupStats {
     unsigned long long max_wdeg_bits;  // non-negative doubles order like their bit patterns
 };
 
+// Maximum degree and maximum weighted degree (as the bit patterns of non-negative doubles, which
+// order like the values) over a warp, then one atomic each from lane 0; every lane of the warp
+// takes part (rows past n contribute zeros).
+__device__ __forceinline__ void warp_max_to(int deg, unsigned long long wbits, SetupStats *stats) {
+    for (int o = 16; o > 0; o >>= 1) {
+        deg = max(deg, __shfl_xor_sync(0xffffffffu, deg, o));
+        const unsigned long long ob = __shfl_xor_sync(0xffffffffu, wbits, o);
+        wbits = ob > wbits ? ob : wbits;
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&stats->max_deg, deg);
+        atomicMax(&stats->max_wdeg_bits, wbits);
+    }
+}
+
 __global__ void k_check_rowptr(int64_t n, int64_t nnz, const int32_t *rp, SetupStats *stats) {
     int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r > n) return;
@@ -176,35 +191,40 @@ __global__ void k_check_rowptr(int64_t n, int64_t nnz, const int32_t *rp, SetupS
 __global__ void k_rows(int64_t n, const int32_t *rp, const int32_t *ci, const float *w, int check,
                        int32_t *cnt_up, SetupStats *stats) {
     int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n) return;
-    int p0 = rp[r], p1 = rp[r + 1];
-    int up = 0, err = 0;
-    double wd = 0.0;
-    int prev = -1;
-    for (int p = p0; p < p1; ++p) {
-        int c = ci[p];
-        if (check) {
-            if (c < 0 || c >= n) err |= CSR_BAD_COL;
-            if (c == r) err |= CSR_SELF_LOOP;
-            if (c <= prev) err |= CSR_UNSORTED;
+    int deg = 0;
+    unsigned long long wbits = 0ull;
+    if (r < n) {
+        int p0 = rp[r], p1 = rp[r + 1];
+        int up = 0, err = 0;
+        double wd = 0.0;
+        int prev = -1;
+        for (int p = p0; p < p1; ++p) {
+            int c = ci[p];
+            if (check) {
+                if (c < 0 || c >= n) err |= CSR_BAD_COL;
+                if (c == r) err |= CSR_SELF_LOOP;
+                if (c <= prev) err |= CSR_UNSORTED;
+            }
+            prev = c;
+            if (c > r) ++up;
+            if (w) {
+                float x = w[p];
+                if (check && !(x >= 0.0f && isfinite(x))) err |= CSR_BAD_WEIGHT;
+                wd += (double)x;
+            } else {
+                wd += 1.0;
+            }
         }
-        prev = c;
-        if (c > r) ++up;
-        if (w) {
-            float x = w[p];
-            if (check && !(x >= 0.0f && isfinite(x))) err |= CSR_BAD_WEIGHT;
-            wd += (double)x;
-        } else {
-            wd += 1.0;
+        cnt_up[r] = up;
+        if (err) {
+            atomicOr(&stats->err, err);
+            atomicMin(&stats->bad_row, (int)r);
         }
+        deg = p1 - p0;
+        wbits = (unsigned long long)__double_as_longlong(wd);
     }
-    cnt_up[r] = up;
-    if (err) {
-        atomicOr(&stats->err, err);
-        atomicMin(&stats->bad_row, (int)r);
-    }
-    atomicMax(&stats->max_deg, p1 - p0);
-    atomicMax(&stats->max_wdeg_bits, (unsigned long long)__double_as_longlong(wd));
+    // the warp's maxima first, then one atomic per warp instead of one per row
+    warp_max_to(deg, wbits, stats);
 }
 
 // Reverse-entry map by binary search in the neighbour's row; symmetric-weight check.
@@ -265,10 +285,17 @@ __global__ void k_edge_weights(int64_t nnz, const int32_t *eid, const float *w_e
 
 __global__ void k_wdeg_max(int64_t n, const int32_t *rp, const float *w, SetupStats *stats) {
     int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n) return;
-    double s = 0.0;
-    for (int p = rp[r]; p < rp[r + 1]; ++p) s += (double)w[p];
-    atomicMax(&stats->max_wdeg_bits, (unsigned long long)__double_as_longlong(s));
+    unsigned long long wbits = 0ull;
+    if (r < n) {
+        double s = 0.0;
+        for (int p = rp[r]; p < rp[r + 1]; ++p) s += (double)w[p];
+        wbits = (unsigned long long)__double_as_longlong(s);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long ob = __shfl_xor_sync(0xffffffffu, wbits, o);
+        wbits = ob > wbits ? ob : wbits;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(&stats->max_wdeg_bits, wbits);
 }
 
 __global__ void k_edge_ends(int64_t ne, const int32_t *ci, const int32_t *edge_p,
