@@ -35,17 +35,25 @@ __global__ void k_eg_util(int k, const double *__restrict__ H, int ldh,
             for (int j = 0; j < i; ++j) S[j * k + i] = -2.0 * H[i * ldh + j] / H[j * ldh + j];
         }
     }
-    __syncthreads();
-    if (threadIdx.x == 0 && Hbar && g) {
-        for (int e = 0; e < k * k; ++e) Hbar[e] = 0.0;
-        for (int a = 0; a < k; ++a) {
-            Hbar[a * k + a] += g[a];
-            for (int j = 0; j < a; ++j) {
-                const double hij = H[a * ldh + j], hjj = H[j * ldh + j];
-                Hbar[a * k + j] += -2.0 * g[a] * hij / hjj;
-                Hbar[j * k + j] += g[a] * hij * hij / (hjj * hjj);
+    // Hbar: row a below the diagonal holds -2 g_a h_aj / h_jj (one term each); the diagonal
+    // entry j is g_j plus the terms g_a h_aj^2 / h_jj^2 of the rows a > j, added in increasing a;
+    // above the diagonal zeros. Thread i writes row i and diagonal entry i.
+    if (i < k && Hbar && g) {
+        for (int j = 0; j < k; ++j) {
+            if (j < i) {
+                const double hij = H[i * ldh + j], hjj = H[j * ldh + j];
+                Hbar[i * k + j] = 0.0 + -2.0 * g[i] * hij / hjj;
+            } else if (j > i) {
+                Hbar[i * k + j] = 0.0;
             }
         }
+        const double hii = H[i * ldh + i];
+        double d = 0.0 + g[i];
+        for (int a = i + 1; a < k; ++a) {
+            const double hai = H[a * ldh + i];
+            d += g[a] * hai * hai / (hii * hii);
+        }
+        Hbar[i * k + i] = d;
     }
 }
 
