@@ -778,7 +778,8 @@ def measure_three_room(sped, torch, dev, stream, k=3, cap_plain=20000, cap_dilat
     of Section 5.3 (s = 2, h = 10: 21 x 61 cells, two walls with one door each), plain reversed
     Laplacian against the dilated operator of degree 251 (limit form), for subspace iteration
     (Oja, eta = 0) and mu-EG, FP64; converged at a largest principal angle <= 1e-3 against the
-    dense eigendecomposition."""
+    dense eigendecomposition; beside it the steps until the eigenvector streak (Section 5.2,
+    eps = pi/8) covers all k eigenvectors, the measure Fig. 1 plots."""
     g = gen.three_room_grid(2, 10)
     n = g.n
     Ld = np.zeros((n, n))
@@ -805,20 +806,31 @@ def measure_three_room(sped, torch, dev, stream, k=3, cap_plain=20000, cap_dilat
         V[:, :k] = V0
         scr = torch.empty(sped.eig_step_scratch_bytes(G, opts, k), dtype=torch.uint8, device=dev)
         every = 1 if cap <= cap_dilated else 10
-        steps, ang = None, None
+        steps, ang, streak_steps, streak = None, None, None, 0
         for t in range(1, cap + 1):
             sped.eig_step(G, V, k, opts, scratch=scr)
             if t % every == 0 or t == cap:
-                ang = _principal_angle(sped, Ud, V, k)
-                if ang <= 1e-3:
-                    steps = t
+                if steps is None:
+                    ang = _principal_angle(sped, Ud, V, k)
+                    if ang <= 1e-3:
+                        steps = t
+                if streak_steps is None:
+                    streak, _ = _streak_device(torch, Ud, V, k, math.pi / 8)
+                    if streak == k:
+                        streak_steps = t
+                if steps is not None and streak_steps is not None:
                     break
         out[name] = {"steps": steps, "spmm": None if steps is None else steps * info.degree,
-                     "final_angle": ang, "eta": e}
+                     "final_angle": ang, "eta": e, "steps_to_full_streak": streak_steps,
+                     "final_streak": streak}
     for sv in ("oja", "mu_eg"):
         p_, d_ = out[f"plain_{sv}"]["steps"], out[f"dilated251_{sv}"]["steps"]
         if p_ and d_:
             out[f"step_ratio_{sv}"] = p_ / d_
+        p_ = out[f"plain_{sv}"]["steps_to_full_streak"]
+        d_ = out[f"dilated251_{sv}"]["steps_to_full_streak"]
+        if p_ and d_:
+            out[f"streak_step_ratio_{sv}"] = p_ / d_
     return out
 
 
