@@ -109,3 +109,26 @@ def test_reference_certificate_matches_the_oracle():
     # the bound holds against the dense eigendecomposition
     ang = oracle.principal_angle_max(U[:, :k], Uk)
     assert np.sin(ang) <= c["davis_kahan_sin_theta_bound"] * (1 + 1e-9)
+
+
+def test_streak_helper_matches_the_oracle():
+    # the benchmark's streak (torch, on whatever device holds the blocks) against the oracle's
+    # definition (Section 5.2) on CPU tensors: leading run of columns within eps of their
+    # eigenvector, sign ignored
+    import math
+    import numpy as np
+    import torch
+    import oracle
+    rng = np.random.default_rng(3)
+    U, _ = np.linalg.qr(rng.standard_normal((60, 5)))
+    for noise, flip in ((1e-3, False), (0.3, True), (0.05, True), (1.0, False)):
+        V = U + noise * rng.standard_normal(U.shape)
+        if flip:
+            V[:, 1] *= -1.0
+        for eps in (math.pi / 8, 0.05):
+            n, ang = bench._streak_device(torch, torch.from_numpy(U), torch.from_numpy(V), 5, eps)
+            assert n == oracle.eigenvector_streak(V, U, eps)
+            for i in range(5):
+                v = V[:, i] / np.linalg.norm(V[:, i])
+                want = math.asin(min(1.0, np.linalg.norm(v - (v @ U[:, i]) * U[:, i])))
+                assert ang[i] == pytest.approx(want, abs=1e-12)
