@@ -1365,6 +1365,19 @@ def run_ours(args, rank, world, local_rank):
                             for a in TTK_ARMS}
             per_seed[sd].update(ttk_ratios(r))
         extra["time_to_bottom_k"]["sbm_n2000_b4_k4_seeds_0_1_2"] = per_seed
+        if args.ttk_seeds:
+            # the near-regular SBM of the benchmark's size with seeds 0, 1, 2 (graph and V0)
+            per_seed = {}
+            for sd in (0, 1, 2):
+                gs = gen.sbm_regular(w["n"], w["blocks"], 14, 2, seed=sd)
+                gs.name = f"sbm_regular_n{w['n']}_b{w['blocks']}_deg14+2_seed{sd}"
+                r = time_to_bottom_k(sped, torch, gs, k, dev, stream, 41, seed=sd)
+                per_seed[sd] = {a: {"steps": r[a]["steps"], "ms": r[a].get("ms")}
+                                for a in TTK_ARMS}
+                per_seed[sd].update(ttk_ratios(r))
+                per_seed[sd]["certificate_sin_bound"] = (
+                    r["reference"].get("certificate", {}).get("davis_kahan_sin_theta_bound"))
+            extra["time_to_bottom_k"]["sbm_regular_n1e6_b20_k20_seeds_0_1_2"] = per_seed
         # the benchmark graph itself, graded at the nearest k >= 20 whose Ritz gap is clear
         extra["time_to_bottom_k"].update(ttk_benchmark_graph(sped, torch, g, G, dev, stream,
                                                              k, ell))
@@ -1488,6 +1501,9 @@ def main():
                          "(0: the degree law's own, about 1.9e8)")
     ap.add_argument("--extras-out", default=None,
                     help="also write every measurement (headline and extras) to this JSON file")
+    ap.add_argument("--ttk-seeds", action="store_true",
+                    help="also run time-to-bottom-k on the near-regular 1e6-node SBM with seeds "
+                         "0, 1, 2 (graph and V0)")
     ap.add_argument("--spectrum", action="store_true",
                     help="print the bottom of the workload's spectrum and exit")
     args = ap.parse_args()
