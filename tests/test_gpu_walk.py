@@ -93,3 +93,28 @@ def test_single_edge_walk_exact_on_gpu():
         torch.cuda.synchronize()
         want = oracle.walk_exact_terms(g, V0, np.array([0.3, -1.0, 0.5, -0.25, 0.125]))
         assert_close(host(Y, k), want, 1e-12)
+
+
+@pytest.mark.parametrize("mode", [sped.STOCHASTIC_IS, sped.STOCHASTIC_REJECT])
+@pytest.mark.parametrize("vt,yt,k,tol", [(torch.float64, torch.float64, 16, 1e-11),
+                                         (torch.float32, torch.float64, 20, 1e-11),
+                                         (torch.float32, torch.float64, 32, 1e-11)])
+def test_walk_several_walkers_per_thread(mode, vt, yt, k, tol):
+    # more walkers than one wave of resident threads (at most 152 SMs x 7 blocks x 128), so every
+    # thread takes several walkers through the grid-stride loop; still walk for walk the oracle's.
+    # FP64 outputs, whose per-walker sums and atomics are FP64: with F32 outputs each row here
+    # takes about 2,400 F32 atomic adds in arbitrary order, a rounding of order 1e-4 per entry
+    # (the F32 tests above bound it at their 20,000 walkers)
+    g = gen.uniform_edge_weights(gen.random_graph(250, 800, seed=5, hub=1, hub_degree=60), seed=6)
+    G = sped.Graph.from_csr(g)
+    G.set_polynomial(sped.POLY_LIMIT_EXP, 5, scale=0.01)
+    c = np.array(G.power_coeffs())
+    V0 = gen.gaussian_block(g.n, k, seed=9)
+    V = to_block(V0, vt)
+    Y = sped.alloc_block(g.n, k, yt, DEV)
+    walkers, seed = 300_001, 24681357
+    sped.apply_poly(G, V, Y, k, mode=mode, walkers=walkers, seed=seed)
+    torch.cuda.synchronize()
+    Vs = torch.from_numpy(V0).to(vt).double().numpy()
+    want = oracle.walk_estimate(g, Vs, c, walkers, seed, mode=mode)
+    assert_close(host(Y, k), want, tol)
