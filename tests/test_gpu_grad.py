@@ -130,3 +130,20 @@ def test_apply_poly_backward_is_the_adjoint(kind):
     assert np.linalg.norm(got - apply(dY0)) <= 1e-12 * np.linalg.norm(got)
     lhs = float(np.sum(dY0 * apply(V0)))
     assert abs(lhs - float(np.sum(got * V0))) <= 1e-10 * abs(lhs)
+
+
+@pytest.mark.parametrize("k", [1, 2, 5, 9, 16, 17, 32])
+@pytest.mark.parametrize("dt,tol", [(torch.float64, 1e-10), (torch.float32, 1e-4)])
+def test_edge_grad_block_widths(k, dt, tol):
+    # the checkpointed SDDMM at every row layout it takes: one to eight 16-byte chunks per row,
+    # partial last chunks, both accumulator widths (k <= 16, k <= 32); every edge against the
+    # oracle's analytic edge gradient of sum_a g_a u_a
+    g, G, info, w, V0 = _setup(n=300, blocks=3, k=k, ell=5, seed=21)
+    Vs = V0.astype(np.float32).astype(np.float64) if dt == torch.float32 else V0
+    V = to_block(Vs, dt)
+    gu = np.linspace(1.0, 0.2, k)
+    Y0 = oracle.poly_limit(g, Vs, info.scale_s, 5)
+    Hb = oracle.eg_utility_hbar(Vs.T @ Y0, gu)
+    got = sped.edge_grad(G, V, k, torch.tensor(Hb.T.copy(), device=DEV)).cpu().numpy()
+    want = oracle.limit_edge_grad(g, Vs, info.scale_s, 5, Hb)
+    assert_close(got, want, tol)
